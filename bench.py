@@ -1,0 +1,325 @@
+"""Benchmark: path-steps/s of the Monte Carlo engine on one GB300 (or N, weak scaling).
+
+A step is one pass of the whole hot path over the workload: path init from
+Philox, n_transient + n_avg predictor-corrector steps of every path with all
+noise increments, the per-path Eq. 31 quotient and the FP64 ensemble
+reduction (sde_run).  Default workload: 2^20 paths of the inertial washboard
+with dichotomous + Gaussian noise, dt = (2 pi / 4.9) / 200, 200 + 2000 periods
+(4.61e11 path-steps per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank runs its own 2^20 paths under its own seed
+(independent shards, no collective on the data path); value = all ranks'
+path-steps / the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "path-steps/s (1 GB300)"
+UNIT = "path-steps/s"
+
+# Algorithmic lane operations per path-step of the inertial model with
+# three-point Gaussian and one jump noise (the method's own arithmetic, counted
+# from Algorithms 1-4 and the Philox definition; derivation in the design doc):
+#   Algorithm 1 on (x, v): 3 drift evaluations x (cos argument 1, SFU cos 1,
+#   force FMA 1, damping FMA 1) = 12, state updates and trapezoid sums 10,
+#   fold of x (scale, round, subtract, count) 4, window sums of v, v^2 2 -> 28
+#   Algorithm 2: one Philox4x32-10 word (10 rounds x 4 ops / 4 words) 10,
+#   three-point selection (2 compares, 2 selects) 4                     -> 14
+#   drive a cos(w t) + F: one table value per step                      ->  1
+#   Algorithm 3/4 countdown (decrement, test, add of the increment)     ->  3
+#   event tail: p = 1 - exp(-mu dt) = 0.0127 x (1/4 Philox 10, log 1,
+#   scale 1, floor 1, guard 3, convert 1, state 2 = 19)                 ->  0.24
+ALG_OPS_PER_PATH_STEP = 46.24
+SM_LANES = 128              # FP32 lanes (= issue slots x 32) per SM
+DEFAULT_SM_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {}, "fallback"
+
+
+def _profile_traffic(workload):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "point_kernel_%s.md" % workload)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+|null)", txt)
+    if not m or m.group(1) == "null":
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_engine(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1409_4923_gb300 import engine as E, workloads as W
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    spec = W.run_spec(args.workload)
+    paths, dt = spec["paths"], spec["dt"]
+    n_tr, n_avg = spec["n_transient"], spec["n_avg"]
+    steps_per_path = n_tr + n_avg
+    stream = torch.cuda.Stream()
+    eng = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
+                   stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+
+    def one_step():
+        eng.run(paths, dt, n_tr, n_avg)
+
+    for _ in range(args.warmup):
+        one_step()
+        eng.stats()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    results = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            evs[i][0].record(stream)
+            one_step()
+            evs[i][1].record(stream)
+            results.append(eng.stats())
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) / 1e3 for a, b in evs]
+    t_total = sum(times)
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    clocks = clk.summary()
+
+    # end to end through the public API with host buffers: create (parameters
+    # from host memory), run, read the statistics back to the host, destroy
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
+                     stream=stream)
+        e.run(paths, dt, n_tr, n_avg)
+        e.stats()
+        e.close()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = statistics.median(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+
+    units = float(paths) * steps_per_path
+    value = units * world * args.steps / t_total
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", DEFAULT_SM_MHZ))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tops = n_sm * SM_LANES * sm_mhz * 1e6 / 1e12
+    kernel_s = statistics.mean(times)
+    achieved = ALG_OPS_PER_PATH_STEP * units / kernel_s / 1e12
+    traffic = _profile_traffic(args.workload)
+    st = results[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Philox seed %d + rank; no dataset in the method)" % spec["seed"],
+        "config": {"workload": args.workload, "paths_per_gpu": paths,
+                   "steps_per_path": steps_per_path, "dt": dt, "n_transient": n_tr,
+                   "n_avg": n_avg, "model": "inertial washboard",
+                   "noise": "gaussian three-point + " + ("dichotomous" if "dichot" in args.workload
+                                                        else "poissonian"),
+                   "parallelism": "paths sharded per GPU" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MiB device write) between timed steps",
+                   "path_arith": "fp32", "accumulators": "fp64"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops,
+                     "unit": "Top/s (lane ops)", "frac": achieved / peak_tops,
+                     "traffic": traffic,
+                     "peak_basis": "%d SMs x %d lanes x %.0f MHz (%s sm_max_mhz)" % (
+                         n_sm, SM_LANES, sm_mhz, peak_kind),
+                     "alg_ops_per_path_step": ALG_OPS_PER_PATH_STEP},
+        # host->device: the parameter record and the fold's item range;
+        # device->host: five FP64 sums and the status word
+        "e2e": {"value": units * world / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": E.ctypes.sizeof(E.Params) + 8,
+                "d2h_bytes_per_step": 5 * 8 + 4},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "result": {"mean_v": st["mean_v"], "stderr_v": st["stderr_v"], "tmean_v": st["tmean_v"],
+                   "tvar_v": st["tvar_v"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
+    eng.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _oracle_sample(spec, paths):
+    import oracle
+    prm = dict(spec["params"])
+    prm["noise"] = prm.pop("noise_flags")
+    p = oracle.make_params(**prm)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.run_paths(spec["model"], p, spec["seed"], 0, paths, spec["dt"], spec["n_transient"],
+                     spec["n_avg"], nthreads=cores)
+    return time.perf_counter() - t0, cores
+
+
+def cpu_baseline(spec, seconds):
+    """The oracle as it stands, on all host cores, over a bounded sample of the
+    same workload (the first paths, full horizon)."""
+    steps = spec["n_transient"] + spec["n_avg"]
+    cores = os.cpu_count() or 1
+    probe = max(1, min(cores, 16))
+    t, _ = _oracle_sample(dict(spec, n_transient=0, n_avg=max(1, steps // 20)), probe)
+    rate = probe * max(1, steps // 20) / t
+    paths = max(cores, int(rate * seconds / steps) // cores * cores)
+    t, cores = _oracle_sample(spec, paths)
+    return {"value": paths * steps / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d paths, full horizon (%d steps), %.1f s wall" % (
+                paths, spec["paths"], steps, t)}
+
+
+def run_reference(args):
+    """The base contract's reference arm: the FP64 CPU oracle, timed as it stands."""
+    from paper_1409_4923_gb300 import workloads as W
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    spec = W.run_spec(args.workload)
+    steps = spec["n_transient"] + spec["n_avg"]
+    cores = os.cpu_count() or 1
+    paths = cores * 2
+    for _ in range(args.warmup):
+        _oracle_sample(dict(spec, n_transient=0, n_avg=steps // 50), cores)
+    times = []
+    for _ in range(args.steps):
+        t, cores = _oracle_sample(spec, paths)
+        times.append(t)
+    value = paths * steps * len(times) / sum(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(times) / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Philox seed %d)" % spec["seed"], "impl": "reference",
+        "config": {"workload": args.workload, "paths_per_step": paths, "steps_per_path": steps,
+                   "dt": spec["dt"], "model": "inertial washboard"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d of %d paths per step, full horizon" % (paths, spec["paths"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="dichot_2p20", choices=["dichot_2p20", "poisson_1024"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * sde.h -- C ABI of the GB300 (sm_103a) Brownian-motor Monte Carlo engine.
+ *
+ * The engine integrates many independent realisations of a Langevin equation
+ * with the jump-adapted simplified weak-order-2.0 predictor-corrector scheme
+ * (Algorithm 1) driven by Gaussian white noise (Algorithm 2, Eq. 25), white
+ * Poissonian noise (Algorithm 3, Eqs. 3-8 and 26-27) and dichotomous noise
+ * (Algorithm 4, Eqs. 13-17 and 29-30), and reduces them to the ensemble
+ * average of Eq. 31 (mean velocity, its variance and standard error) and to
+ * time-and-ensemble velocity moments.  Every step of that path runs in the
+ * library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Models (x is the coordinate, V = V0 sin(2 pi x) has period L = 1, the
+ * piecewise-linear V of Eq. 2 has period L = 2):
+ *   SDE_INERTIAL_WASHBOARD    x' = v,
+ *                             v' = -gamma v - V'(x) + a cos(omega t) + F
+ *                                  + sqrt(2 gamma Q) xi(t) + eta(t) + Gamma(t)
+ *   SDE_OVERDAMPED_WASHBOARD  x' = -V'(x) + a cos(omega t) + F
+ *                                  + sqrt(2 Q) xi(t) + eta(t) + Gamma(t)
+ *   SDE_OVERDAMPED_PWL        as the previous line with V of Eq. 2 (Eq. 24;
+ *                             Models I and II are its limits, Eqs. 1 and 12)
+ * Noise is added to v (inertial) or x (overdamped).  The Poissonian and
+ * dichotomous increments enter only the corrector (Algorithm 1 line 6).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit seed,
+ * counter = (index_lo, tag << 30 | point, path, index_hi); tag 0 initial
+ * state, 1 Gaussian (word n & 3 of index n >> 2 serves step n), 2 Poisson
+ * (event j: words 2(j&1), 2(j&1)+1 of index j >> 1), 3 dichotomous (event j:
+ * word j & 3 of index j >> 2).  Uniforms are phi = (w >> 8) 2^-24 in [0,1) and
+ * u = 1 - phi in (0,1].  Results are a pure function of (model, parameters,
+ * seed, path count, dt, step counts); they do not depend on the launch shape.
+ *
+ * Errors: every int-returning call returns 0 on success or a negative SDE_E*
+ * code; sde_last_error() gives the message.  Nothing throws across the ABI.
+ * Threading: one context must not be used from two host threads at once.
+ */
+#ifndef SDE_H
+#define SDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDE_OK         0
+#define SDE_EINVAL    -1   /* invalid argument (NaN parameter, dt <= 0, ...) */
+#define SDE_ECUDA     -2   /* a CUDA call failed (message names it)           */
+#define SDE_ENOMEM    -3   /* device or host allocation failed                */
+#define SDE_ETIMEDOUT -4   /* the device-side deadline expired before the end */
+#define SDE_ESTATE    -5   /* call out of order (e.g. stats before run)        */
+
+typedef enum {
+    SDE_INERTIAL_WASHBOARD = 0,
+    SDE_OVERDAMPED_WASHBOARD = 1,
+    SDE_OVERDAMPED_PWL = 2
+} sde_model;
+
+/* noise_flags */
+#define SDE_NOISE_GAUSS       1u   /* Gaussian white noise, intensity Q          */
+#define SDE_NOISE_POISSON     2u   /* white Poissonian noise (lambda, zeta)      */
+#define SDE_NOISE_DICHOT      4u   /* dichotomous noise (-Fa, Fb; mua, mub)      */
+#define SDE_GAUSS_NORMAL      8u   /* Gaussian increments instead of Eq. 25      */
+#define SDE_POIS_COMPENSATED 16u   /* bias a = zeta (1 - e^{-lambda dt}) / dt    */
+                                   /* instead of Eq. 6's lambda zeta             */
+
+/* Parameters of one point of parameter space.  Plain old data; the library
+ * copies it at the call.  Rates and intensities must be finite and >= 0;
+ * lambda > 0 and zeta > 0 with SDE_NOISE_POISSON; Fa, Fb >= 0 and mua,
+ * mub > 0 with SDE_NOISE_DICHOT.  The initial state of path i is
+ * x0 = x0_lo + (x0_hi - x0_lo) phi, v0 = v0_lo + (v0_hi - v0_lo) phi', and
+ * the dichotomous state starts in F_b with probability mua / (mua + mub). */
+typedef struct {
+    double gamma, a, omega, F, Q;   /* damping, drive amplitude/frequency, bias, D_G */
+    double lambda, zeta;            /* Poisson rate and mean amplitude (Eqs. 4-5)   */
+    double Fa, Fb, mua, mub;        /* dichotomous levels and rates (Eqs. 13-14)    */
+    double V0;                      /* amplitude of the potential                   */
+    double x0_lo, x0_hi, v0_lo, v0_hi;
+    uint32_t noise_flags;
+    uint32_t point;                 /* point id in the random counter, < 2^30       */
+} sde_params;
+
+/* Ensemble statistics of one run (Eq. 31 and time averages). */
+typedef struct {
+    uint64_t n;        /* number of paths                                       */
+    double mean_v;     /* <(x(t_f) - x(t_i)) / (t_f - t_i)>  (Eq. 31)           */
+    double var_v;      /* sample variance of the per-path quotient              */
+    double stderr_v;   /* sqrt(var_v / n)                                       */
+    double tmean_v;    /* time-and-ensemble mean of v over the averaging window  */
+    double tvar_v;     /* time-and-ensemble variance of v (inertial model only) */
+    double sums[5];    /* device FP64 sums: n, sum vbar, sum vbar^2, sum v, sum v^2 */
+    int32_t status;    /* SDE_OK or SDE_ETIMEDOUT                               */
+    int32_t pad;
+} sde_stats_t;
+
+/* Optional per-path outputs, all DEVICE pointers of length `paths` (any may
+ * be NULL).  X_f: unfolded final position; v_f: final velocity (inertial);
+ * vbar: per-path Eq. 31 quotient; jP, jD: index of the last Poisson /
+ * dichotomous event drawn (0 = only the initial countdown). */
+typedef struct {
+    double* X_f;
+    float* v_f;
+    double* vbar;
+    uint32_t* jP;
+    uint32_t* jD;
+} sde_path_out;
+
+typedef struct sde_ctx sde_ctx;
+
+/* Create a context for `model` with parameters `p` (copied) and `seed`, bound
+ * to the CUDA stream `cuda_stream` (a cudaStream_t, borrowed; NULL = legacy
+ * default stream) on the current device.  The context owns its device
+ * workspace, which grows on demand and is released by sde_destroy.
+ * Parameter meaning: Sec. 3 (Eqs. 1-17) and the model list above. */
+int sde_create(sde_ctx** out, sde_model model, const sde_params* p, uint64_t seed,
+               void* cuda_stream);
+
+/* Replace the parameters of an existing context (validated, copied). */
+int sde_set_params(sde_ctx* ctx, const sde_params* p);
+
+/* Enqueue one Monte Carlo run on the context's stream: `paths` independent
+ * realisations, each integrated for n_transient + n_avg steps of dt from the
+ * initial law above (Algorithm 5: one path per GPU lane, state in registers),
+ * then reduced per Eq. 31 with t_i = n_transient dt and t_f = t_i + n_avg dt.
+ * Asynchronous: returns after the launches.  paths in [1, 2^32), dt > 0,
+ * n_avg >= 1.  EINVAL on bad arguments, ENOMEM / ECUDA on device failure. */
+int sde_run(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_transient, uint64_t n_avg);
+
+/* As sde_run, additionally writing per-path results to `out` (device memory
+ * owned by the caller, each array of length `paths`). */
+int sde_run_paths(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_transient,
+                  uint64_t n_avg, const sde_path_out* out);
+
+/* Wait for the last run on the context's stream and return its statistics
+ * (host struct `out`).  ESTATE if no run was enqueued. */
+int sde_stats(sde_ctx* ctx, sde_stats_t* out);
+
+/* One point of a batched parameter scan: parameters, step size, path count
+ * and step counts (transient, averaged). */
+typedef struct {
+    sde_params p;
+    double dt;
+    uint64_t paths;
+    uint64_t n_transient;
+    uint64_t n_avg;
+} sde_scan_point;
+
+/* Batched scan (Sec. 5: many parameter values in one kernel call): all
+ * `npts` points (host array, copied) run in one persistent launch over
+ * (point, 32-path tile) work items ordered longest first, replayed from a
+ * CUDA graph when the shape repeats, and folded per point in a fixed order.
+ * All points share the context's model; each point's noise_flags must equal
+ * those of the first point.  Writes npts statistics to the host array `out`
+ * (synchronises the stream).  deadline_ms > 0 bounds the device time: work
+ * items not started by then are skipped and every point's status becomes
+ * SDE_ETIMEDOUT (the call then returns SDE_ETIMEDOUT). */
+int sde_scan(sde_ctx* ctx, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out,
+             double deadline_ms);
+
+/* Reduce `n` device doubles `vals` to {n, sum, sum of squares} with the same
+ * FP64 fold the engine uses (pairwise within a warp, Kahan across items).
+ * `out3` is a host array of three doubles.  Synchronises the stream. */
+int sde_reduce_f64(sde_ctx* ctx, const double* vals, uint64_t n, double* out3);
+
+/* Words of the engine's device Philox4x32-10 for counters ctr[4*i..4*i+3]
+ * (host array) and key (seed): writes 4*n words to the host array `out`.
+ * Runs on the device; exposed so the stream contract can be tested. */
+int sde_philox_words(sde_ctx* ctx, const uint32_t* ctr, uint64_t n, uint64_t seed,
+                     uint32_t* out);
+
+/* Launch shape of the path kernels of this context: threads per block
+ * (32..128, multiple of 32) and blocks in the grid (0 = one persistent wave
+ * from the occupancy calculator).  Results never depend on the shape; the
+ * autotuner of the Python layer picks it.  EINVAL outside those ranges. */
+int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
+
+/* Resident blocks per SM of this context's path kernel at `block_threads`,
+ * and the device's SM count (host outputs). */
+int sde_occupancy(sde_ctx* ctx, int block_threads, int* blocks_per_sm, int* sm_count);
+
+/* Free everything the context owns (waits for its stream first). */
+void sde_destroy(sde_ctx* ctx);
+
+/* Message of the last error on `ctx` (or of the last failed sde_create when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char* sde_last_error(const sde_ctx* ctx);
+
+/* Library version string. */
+const char* sde_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

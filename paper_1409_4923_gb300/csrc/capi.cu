@@ -1,0 +1,564 @@
+// capi.cu -- host runtime of the engine behind the C ABI of include/sde.h.
+//
+// The context validates parameters, turns them into FP32/FP64 kernel
+// constants once (in FP64 on the host), owns a grow-only device workspace and
+// a pinned result buffer, and enqueues: counter reset -> persistent path
+// kernel -> fixed-order FP64 fold -> 40-byte device-to-host copy.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sde.h"
+#include "launch.h"
+
+using namespace sde;
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr uint32_t kMaxSteps = 0xFFFFFF00u;   // n_transient + n_avg, keeps 32-bit step indices
+
+struct ScanGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct sde_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    sde_model model = SDE_INERTIAL_WASHBOARD;
+    sde_params p{};
+    uint64_t seed = 0;
+    std::string err;
+    // device workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // pinned host results
+    double* host = nullptr;
+    size_t host_bytes = 0;
+    cudaEvent_t done = nullptr;
+    bool has_run = false;
+    uint64_t last_paths = 0;
+    uint64_t last_n_avg = 0;
+    // tuning
+    int block_threads = 128;
+    int grid_blocks = 0;          // 0 = persistent grid from occupancy
+    // scan graphs keyed by (npts, n_items, flags, budget)
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, ScanGraph> graphs;
+};
+
+static std::string g_create_error;
+
+static int fail(sde_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg; else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(sde_ctx* c, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? SDE_ENOMEM : SDE_ECUDA, m);
+}
+
+#define SDE_CUDA(c, call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); } while (0)
+
+static bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+static int validate_params(sde_ctx* c, sde_model model, const sde_params* p)
+{
+    if (!p) return fail(c, SDE_EINVAL, "params is NULL");
+    if ((int)model < 0 || (int)model > 2) return fail(c, SDE_EINVAL, "unknown model");
+    const double all[] = {p->gamma, p->a, p->omega, p->F, p->Q, p->lambda, p->zeta, p->Fa, p->Fb,
+                          p->mua, p->mub, p->V0, p->x0_lo, p->x0_hi, p->v0_lo, p->v0_hi};
+    for (double x : all)
+        if (!std::isfinite(x)) return fail(c, SDE_EINVAL, "non-finite parameter");
+    if (!finite_nonneg(p->Q)) return fail(c, SDE_EINVAL, "Q must be >= 0");
+    if (model == SDE_INERTIAL_WASHBOARD && !(p->gamma > 0.0))
+        return fail(c, SDE_EINVAL, "gamma must be > 0 for the inertial model");
+    if (p->noise_flags & ~31u) return fail(c, SDE_EINVAL, "unknown noise flag");
+    if ((p->noise_flags & SDE_NOISE_POISSON) && !(p->lambda > 0.0 && p->zeta > 0.0))
+        return fail(c, SDE_EINVAL, "Poisson noise needs lambda > 0 and zeta > 0");
+    if ((p->noise_flags & SDE_NOISE_DICHOT) &&
+        !(p->mua > 0.0 && p->mub > 0.0 && p->Fa >= 0.0 && p->Fb >= 0.0))
+        return fail(c, SDE_EINVAL, "dichotomous noise needs mua, mub > 0 and Fa, Fb >= 0");
+    if (p->point >= (1u << 30)) return fail(c, SDE_EINVAL, "point id must be < 2^30");
+    return SDE_OK;
+}
+
+static int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
+{
+    if (paths < 1 || paths > 0xFFFFFFC0ull) return fail(c, SDE_EINVAL, "paths must be in [1, 2^32 - 64]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDE_EINVAL, "dt must be finite and > 0");
+    if (n_avg < 1) return fail(c, SDE_EINVAL, "n_avg must be >= 1");
+    if (n_tr > kMaxSteps || n_avg > kMaxSteps || n_tr + n_avg > kMaxSteps)
+        return fail(c, SDE_EINVAL, "n_transient + n_avg must be < 2^32 - 256");
+    return SDE_OK;
+}
+
+static int gauss_kind(uint32_t flags) { return (flags & SDE_GAUSS_NORMAL) ? kGaussNormal : kGauss3Point; }
+
+// Kernel constants of one point, from the FP64 parameters.  Coordinates:
+// washboards integrate c = 2 pi x (so the SFU cosine takes c directly), the
+// piecewise-linear model integrates x; noise is scaled into those units.
+static int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,
+                      uint64_t n_tr, uint64_t n_avg, uint32_t first_item, PointConsts& P)
+{
+    std::memset(&P, 0, sizeof(P));
+    const bool inertial = model == SDE_INERTIAL_WASHBOARD;
+    const bool pwl = model == SDE_OVERDAMPED_PWL;
+    const double cs = pwl ? 1.0 : kTwoPi;             // coordinate per unit x
+    const double ns = inertial ? 1.0 : cs;            // noise acts on v (inertial) or the coordinate
+    const uint32_t f = p.noise_flags;
+
+    P.gdt = (float)(p.gamma * dt);
+    if (inertial) P.fdt = (float)(p.V0 * kTwoPi * dt);
+    else if (pwl) P.fdt = (float)(p.V0 * dt);
+    else P.fdt = (float)(p.V0 * kTwoPi * cs * dt);
+    P.wdt = (float)(cs * dt);
+    P.whdt = (float)(0.5 * cs * dt);
+    const double dscale = inertial ? dt : cs * dt;
+    P.a_dt = (float)(p.a * dscale);
+    P.F_dt = (float)(p.F * dscale);
+    double frac = p.omega * dt / kTwoPi;
+    frac -= std::floor(frac);
+    double fx = std::ldexp(frac, 64);
+    P.phase_step = fx >= 18446744073709551615.0 ? 0ull : (uint64_t)fx;
+
+    const double G = inertial ? std::sqrt(2.0 * p.gamma * p.Q) : std::sqrt(2.0 * p.Q);
+    P.gauss_on = (f & SDE_NOISE_GAUSS) && G > 0.0 ? 1u : 0u;
+    P.xi_c = (float)(ns * G * ((f & SDE_GAUSS_NORMAL) ? std::sqrt(dt) : std::sqrt(3.0 * dt)));
+    if (f & SDE_NOISE_POISSON) {
+        const double aP = (f & SDE_POIS_COMPENSATED) ? p.zeta * (-std::expm1(-p.lambda * dt)) / dt
+                                                     : p.lambda * p.zeta;
+        if (p.lambda * dt < 1e-8) return fail(c, SDE_EINVAL, "lambda dt must be >= 1e-8");
+        P.aP_dt = (float)(ns * aP * dt);
+        P.zeta_l2 = (float)(ns * p.zeta * M_LN2);
+        P.pois_cl2 = (float)(M_LN2 / (p.lambda * dt));
+        P.inv_lambda = 1.0 / p.lambda;
+    }
+    if (f & SDE_NOISE_DICHOT) {
+        if (p.mua * dt < 1e-8 || p.mub * dt < 1e-8) return fail(c, SDE_EINVAL, "mu dt must be >= 1e-8");
+        P.Fb_dt = (float)(ns * p.Fb * dt);
+        P.mFa_dt = (float)(-ns * p.Fa * dt);
+        P.mua_cl2 = (float)(M_LN2 / (p.mua * dt));
+        P.mub_cl2 = (float)(M_LN2 / (p.mub * dt));
+        P.inv_mua = 1.0 / p.mua;
+        P.inv_mub = 1.0 / p.mub;
+        // d0 = F_b iff (w >> 8) 2^-24 < mua / (mua + mub)  <=>  (w >> 8) < ceil(thr 2^24)
+        const double thr = p.mua / (p.mua + p.mub);
+        P.d0_thresh = (uint32_t)std::ceil(std::ldexp(thr, 24));
+    }
+    P.dt64 = dt;
+    P.x0_lo = (float)p.x0_lo;
+    P.x0_span = (float)(p.x0_hi - p.x0_lo);
+    P.v0_lo = (float)p.v0_lo;
+    P.v0_span = (float)(p.v0_hi - p.v0_lo);
+    P.c1_init = (kTagInit << 30) | p.point;
+    P.c1_gauss = (kTagGauss << 30) | p.point;
+    P.c1_pois = (kTagPois << 30) | p.point;
+    P.c1_dich = (kTagDich << 30) | p.point;
+    P.n_tr = (uint32_t)n_tr;
+    P.n_avg = (uint32_t)n_avg;
+    P.n_paths = (uint32_t)paths;
+    P.first_item = first_item;
+    P.inv_window = 1.0 / ((double)n_avg * dt);
+    // the fold subtracts FP32 multiples of the period constant; the unfolded
+    // coordinate therefore advances by that constant per folded period
+    P.period = pwl ? 2.0 : (double)6.2831853071795865f / kTwoPi;
+    P.coord_to_x = pwl ? 1.0 : 1.0 / kTwoPi;
+    return SDE_OK;
+}
+
+static LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns)
+{
+    LaunchConsts K;
+    std::memset(&K, 0, sizeof(K));
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.rk0[r] = k0;
+        K.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    K.n_items = n_items;
+    K.single_point = 1;
+    K.budget_ns = budget_ns;
+    return K;
+}
+
+// Cached scan graphs bake workspace and pinned-buffer addresses.
+static void drop_graphs(sde_ctx* c)
+{
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c->graphs.clear();
+}
+
+static int ensure_ws(sde_ctx* c, size_t bytes)
+{
+    if (bytes <= c->ws_bytes) return SDE_OK;
+    drop_graphs(c);
+    if (c->ws) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    size_t want = std::max(bytes, c->ws_bytes * 2);
+    SDE_CUDA(c, cudaMalloc(&c->ws, want));
+    c->ws_bytes = want;
+    return SDE_OK;
+}
+
+static int ensure_host(sde_ctx* c, size_t bytes)
+{
+    if (bytes <= c->host_bytes) return SDE_OK;
+    drop_graphs(c);
+    if (c->host) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->host);
+        c->host = nullptr;
+        c->host_bytes = 0;
+    }
+    SDE_CUDA(c, cudaMallocHost((void**)&c->host, bytes));
+    c->host_bytes = bytes;
+    return SDE_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255u) & ~(size_t)255u; }
+
+// Workspace layout: [counter u32, status i32 | ranges uint2[npts] | out5 f64[5 npts] |
+//                    partials f64[5 items] | extra]
+struct Layout {
+    size_t off_ranges, off_out5, off_partials, off_extra, total;
+};
+
+static Layout layout(uint32_t npts, uint64_t items, size_t extra)
+{
+    Layout L;
+    L.off_ranges = 256;
+    L.off_out5 = L.off_ranges + align256(sizeof(uint2) * npts);
+    L.off_partials = L.off_out5 + align256(sizeof(double) * 5 * npts);
+    L.off_extra = L.off_partials + align256(sizeof(double) * 5 * items);
+    L.total = L.off_extra + align256(extra);
+    return L;
+}
+
+static void fill_stats(const double* s5, int32_t status, uint64_t n_avg, sde_stats_t* o)
+{
+    std::memset(o, 0, sizeof(*o));
+    for (int i = 0; i < 5; ++i) o->sums[i] = s5[i];
+    const double n = s5[0];
+    o->n = (uint64_t)n;
+    if (n > 0) {
+        o->mean_v = s5[1] / n;
+        o->var_v = n > 1 ? std::max(0.0, (s5[2] - n * o->mean_v * o->mean_v) / (n - 1.0)) : 0.0;
+        o->stderr_v = std::sqrt(o->var_v / n);
+        const double cnt = n * (double)n_avg;
+        o->tmean_v = s5[3] / cnt;
+        o->tvar_v = s5[4] / cnt - o->tmean_v * o->tmean_v;
+    }
+    o->status = status;
+}
+
+extern "C" {
+
+const char* sde_version(void) { return "sde-gb300 1.0 (sm_103a)"; }
+
+const char* sde_last_error(const sde_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int sde_create(sde_ctx** out, sde_model model, const sde_params* p, uint64_t seed, void* cuda_stream)
+{
+    if (!out) return fail(nullptr, SDE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_params(nullptr, model, p);
+    if (rc) return rc;
+    sde_ctx* c = new (std::nothrow) sde_ctx();
+    if (!c) return fail(nullptr, SDE_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess && cuda_stream == nullptr) {
+        e = cudaStreamCreate(&c->stream);
+        c->own_stream = e == cudaSuccess;
+    } else {
+        c->stream = (cudaStream_t)cuda_stream;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "sde_create");
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? SDE_ENOMEM : SDE_ECUDA;
+    }
+    c->model = model;
+    c->p = *p;
+    c->seed = seed;
+    *out = c;
+    return SDE_OK;
+}
+
+int sde_set_params(sde_ctx* c, const sde_params* p)
+{
+    if (!c) return SDE_EINVAL;
+    int rc = validate_params(c, c->model, p);
+    if (rc) return rc;
+    c->p = *p;
+    return SDE_OK;
+}
+
+int sde_set_tuning(sde_ctx* c, int block_threads, int grid_blocks)
+{
+    if (!c) return SDE_EINVAL;
+    if (block_threads < 32 || block_threads > 128 || block_threads % 32)
+        return fail(c, SDE_EINVAL, "block_threads must be 32, 64, 96 or 128");
+    if (grid_blocks < 0) return fail(c, SDE_EINVAL, "grid_blocks must be >= 0");
+    c->block_threads = block_threads;
+    c->grid_blocks = grid_blocks;
+    return SDE_OK;
+}
+
+int sde_occupancy(sde_ctx* c, int block_threads, int* blocks_per_sm, int* sm_count)
+{
+    if (!c || !blocks_per_sm || !sm_count) return SDE_EINVAL;
+    const uint32_t f = c->p.noise_flags;
+    *blocks_per_sm = point_blocks_per_sm((int)c->model, (f & SDE_NOISE_POISSON) != 0,
+                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(f), block_threads);
+    *sm_count = c->sm_count;
+    return SDE_OK;
+}
+
+static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg,
+                    const sde_path_out* out)
+{
+    if (!c) return SDE_EINVAL;
+    int rc = validate_run(c, paths, dt, n_tr, n_avg);
+    if (rc) return rc;
+    const uint64_t items = (paths + 31ull) / 32ull;
+    PointConsts P;
+    rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, 0u, P);
+    if (rc) return rc;
+    const Layout L = layout(1, items, 0);
+    if ((rc = ensure_ws(c, L.total))) return rc;
+    if ((rc = ensure_host(c, 64))) return rc;
+    char* base = (char*)c->ws;
+    Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
+    uint2* ranges = (uint2*)(base + L.off_ranges);
+    double* out5 = (double*)(base + L.off_out5);
+    const uint2 r0 = make_uint2(0u, (uint32_t)items);
+    SDE_CUDA(c, cudaMemsetAsync(base, 0, 8, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(ranges, &r0, sizeof(r0), cudaMemcpyHostToDevice, c->stream));
+    PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (out) po = PathOutPtrs{out->X_f, out->v_f, out->vbar, out->jP, out->jD};
+    const LaunchConsts K = make_launch(c->seed, (uint32_t)items, 0);
+    const uint32_t f = c->p.noise_flags;
+    SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+                             gauss_kind(f), P, K, ws, po, c->block_threads, c->grid_blocks,
+                             c->sm_count, c->stream));
+    SDE_CUDA(c, launch_fold(ws.partials, ranges, 1, out5, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(c->host, out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(c->host + 5, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaEventRecord(c->done, c->stream));
+    c->has_run = true;
+    c->last_paths = paths;
+    c->last_n_avg = n_avg;
+    return SDE_OK;
+}
+
+int sde_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
+{
+    return run_impl(c, paths, dt, n_tr, n_avg, nullptr);
+}
+
+int sde_run_paths(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg,
+                  const sde_path_out* out)
+{
+    return run_impl(c, paths, dt, n_tr, n_avg, out);
+}
+
+int sde_stats(sde_ctx* c, sde_stats_t* out)
+{
+    if (!c || !out) return SDE_EINVAL;
+    if (!c->has_run) return fail(c, SDE_ESTATE, "sde_stats before sde_run");
+    SDE_CUDA(c, cudaEventSynchronize(c->done));
+    int32_t status;
+    std::memcpy(&status, c->host + 5, sizeof(status));
+    fill_stats(c->host, status, c->last_n_avg, out);
+    return status == kStatusOk ? SDE_OK : fail(c, SDE_ETIMEDOUT, "device deadline expired");
+}
+
+int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out, double deadline_ms)
+{
+    if (!c || (!pts && npts) || (!out && npts)) return SDE_EINVAL;
+    if (npts == 0) return SDE_OK;
+    if (!(deadline_ms >= 0.0) || !std::isfinite(deadline_ms)) return fail(c, SDE_EINVAL, "deadline_ms must be >= 0");
+    const uint32_t flags = pts[0].p.noise_flags;
+    std::vector<PointConsts> P(npts);
+    std::vector<uint64_t> steps(npts);
+    for (uint32_t i = 0; i < npts; ++i) {
+        int rc = validate_params(c, c->model, &pts[i].p);
+        if (rc) return rc;
+        if (pts[i].p.noise_flags != flags) return fail(c, SDE_EINVAL, "all scan points need the same noise flags");
+        if ((rc = validate_run(c, pts[i].paths, pts[i].dt, pts[i].n_transient, pts[i].n_avg))) return rc;
+        steps[i] = pts[i].n_transient + pts[i].n_avg;
+    }
+    const uint64_t budget = (uint64_t)(deadline_ms * 1e6);
+    // longest-processing-time-first order of points; items of a point stay contiguous
+    std::vector<uint32_t> order(npts);
+    for (uint32_t i = 0; i < npts; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return steps[a] > steps[b]; });
+    std::vector<uint2> ranges(npts), items;
+    uint64_t total_items = 0;
+    for (uint32_t i = 0; i < npts; ++i) total_items += (pts[i].paths + 31ull) / 32ull;
+    if (total_items > 0xFFFFFF00ull) return fail(c, SDE_EINVAL, "too many work items");
+    items.reserve(total_items);
+    for (uint32_t k = 0; k < npts; ++k) {
+        const uint32_t i = order[k];
+        const uint32_t first = (uint32_t)items.size();
+        const uint64_t ni = (pts[i].paths + 31ull) / 32ull;
+        for (uint64_t t = 0; t < ni; ++t) items.push_back(make_uint2(i, (uint32_t)(32ull * t)));
+        ranges[i] = make_uint2(first, (uint32_t)ni);
+        int rc = make_point(c, c->model, pts[i].p, pts[i].dt, pts[i].paths, pts[i].n_transient,
+                            pts[i].n_avg, first, P[i]);
+        if (rc) return rc;
+    }
+    const bool use_scan_kernel = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
+    const size_t extra = align256(sizeof(PointConsts) * npts) + align256(sizeof(uint2) * total_items);
+    const Layout L = layout(npts, total_items, extra);
+    int rc;
+    if ((rc = ensure_ws(c, L.total))) return rc;
+    const size_t host_need = sizeof(double) * 5 * npts + 64;
+    if ((rc = ensure_host(c, host_need))) return rc;
+    char* base = (char*)c->ws;
+    Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
+    uint2* d_ranges = (uint2*)(base + L.off_ranges);
+    double* d_out5 = (double*)(base + L.off_out5);
+    PointConsts* d_pts = (PointConsts*)(base + L.off_extra);
+    uint2* d_items = (uint2*)(base + L.off_extra + align256(sizeof(PointConsts) * npts));
+    SDE_CUDA(c, cudaMemcpyAsync(d_pts, P.data(), sizeof(PointConsts) * npts, cudaMemcpyHostToDevice, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(d_items, items.data(), sizeof(uint2) * total_items, cudaMemcpyHostToDevice, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(d_ranges, ranges.data(), sizeof(uint2) * npts, cudaMemcpyHostToDevice, c->stream));
+    double* h_out = c->host;
+    int32_t* h_status = (int32_t*)(c->host + 5 * npts);
+    if (use_scan_kernel) {
+        const LaunchConsts K = make_launch(c->seed, (uint32_t)total_items, budget);
+        auto key = std::make_tuple(npts, (uint32_t)total_items, flags, budget);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end() || c->stream == nullptr) {
+            ScanGraph g;
+            bool capture = c->stream != nullptr;
+            if (capture) SDE_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaMemsetAsync(base, 0, 8, c->stream);
+            if (e == cudaSuccess)
+                e = launch_scan((flags & SDE_NOISE_POISSON) != 0, (flags & SDE_NOISE_DICHOT) != 0, d_pts,
+                                d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream);
+            if (e == cudaSuccess) e = launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * npts, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+            if (capture) {
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &g.graph);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+                if (e != cudaSuccess) {
+                    if (g.graph) cudaGraphDestroy(g.graph);
+                    return cuda_fail(c, e, "scan graph capture");
+                }
+                c->graphs[key] = g;
+                SDE_CUDA(c, cudaGraphLaunch(g.exec, c->stream));
+            } else if (e != cudaSuccess) {
+                return cuda_fail(c, e, "scan launch");
+            }
+        } else {
+            SDE_CUDA(c, cudaGraphLaunch(it->second.exec, c->stream));
+        }
+    } else {
+        // other models: one point-kernel launch per point, same fold
+        SDE_CUDA(c, cudaMemsetAsync(base + 4, 0, 4, c->stream));
+        for (uint32_t i = 0; i < npts; ++i) {
+            const LaunchConsts K = make_launch(c->seed, ranges[i].y, budget);
+            Workspace wsi{ws.counter, ws.status, ws.partials + 5ull * ranges[i].x};
+            SDE_CUDA(c, cudaMemsetAsync(base, 0, 4, c->stream));
+            PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
+            SDE_CUDA(c, launch_point((int)c->model, (flags & SDE_NOISE_POISSON) != 0,
+                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(flags), P[i], K, wsi,
+                                     po, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+        }
+        SDE_CUDA(c, launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream));
+        SDE_CUDA(c, cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * npts, cudaMemcpyDeviceToHost, c->stream));
+        SDE_CUDA(c, cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int32_t status = *h_status;
+    for (uint32_t i = 0; i < npts; ++i) fill_stats(h_out + 5ull * i, status, pts[i].n_avg, &out[i]);
+    return status == kStatusOk ? SDE_OK : fail(c, SDE_ETIMEDOUT, "device deadline expired");
+}
+
+int sde_reduce_f64(sde_ctx* c, const double* vals, uint64_t n, double* out3)
+{
+    if (!c || (!vals && n) || !out3) return SDE_EINVAL;
+    if (n > 0xFFFFFFFFull * 32ull) return fail(c, SDE_EINVAL, "n too large");
+    const uint64_t items = (n + 31ull) / 32ull;
+    const Layout L = layout(1, items, 0);
+    int rc;
+    if ((rc = ensure_ws(c, L.total))) return rc;
+    if ((rc = ensure_host(c, 64))) return rc;
+    char* base = (char*)c->ws;
+    double* partials = (double*)(base + L.off_partials);
+    uint2* ranges = (uint2*)(base + L.off_ranges);
+    double* out5 = (double*)(base + L.off_out5);
+    const uint2 r0 = make_uint2(0u, (uint32_t)items);
+    SDE_CUDA(c, cudaMemcpyAsync(ranges, &r0, sizeof(r0), cudaMemcpyHostToDevice, c->stream));
+    SDE_CUDA(c, launch_reduce_items(vals, n, partials, c->stream));
+    SDE_CUDA(c, launch_fold(partials, ranges, 1, out5, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(c->host, out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    out3[0] = c->host[0];
+    out3[1] = c->host[1];
+    out3[2] = c->host[2];
+    return SDE_OK;
+}
+
+int sde_philox_words(sde_ctx* c, const uint32_t* ctr, uint64_t n, uint64_t seed, uint32_t* out)
+{
+    if (!c || (!ctr && n) || (!out && n)) return SDE_EINVAL;
+    if (n == 0) return SDE_OK;
+    if (n > (1ull << 26)) return fail(c, SDE_EINVAL, "n too large");
+    const size_t bytes = align256(16 * n);
+    int rc;
+    if ((rc = ensure_ws(c, 2 * bytes))) return rc;
+    uint4* d_in = (uint4*)c->ws;
+    uint4* d_out = (uint4*)((char*)c->ws + bytes);
+    SDE_CUDA(c, cudaMemcpyAsync(d_in, ctr, 16 * n, cudaMemcpyHostToDevice, c->stream));
+    const LaunchConsts K = make_launch(seed, 0, 0);
+    SDE_CUDA(c, launch_philox(d_in, n, K, d_out, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(out, d_out, 16 * n, cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SDE_OK;
+}
+
+void sde_destroy(sde_ctx* c)
+{
+    if (!c) return;
+    if (c->stream || c->own_stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->ws) cudaFree(c->ws);
+    if (c->host) cudaFreeHost(c->host);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,476 @@
+// engine.cuh -- device code of the Brownian-motor Monte Carlo engine (sm_103a).
+//
+// One GPU lane integrates one path (Algorithm 5 of the paper: the path state
+// lives in registers for the whole run).  Paths are grouped in 32-path warp
+// items pulled from a work counter, so a warp never waits for another warp and
+// the ensemble reduction (Eq. 31) is a warp-shuffle tree per item plus a
+// fixed-order FP64 fold per parameter point.
+//
+// Arithmetic: the path state and the step arithmetic are FP32 (Sec. 5,
+// "use single precision ... folding of x"); the per-path window accumulators
+// and every ensemble sum are FP64; the phase of the periodic drive is a 64-bit
+// fixed-point fraction of a period, so it wraps modulo 2 pi exactly.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sde {
+
+enum : uint32_t { kTagInit = 0u, kTagGauss = 1u, kTagPois = 2u, kTagDich = 3u };
+enum { kModelInertial = 0, kModelOverdampedWashboard = 1, kModelPWL = 2 };
+enum { kGauss3Point = 1, kGaussNormal = 2 };
+enum : int32_t { kStatusOk = 0, kStatusTimedOut = -4 };
+
+// ---------------------------------------------------------------- parameters
+
+// Per-launch constants (kernel argument, read from the constant bank).
+struct LaunchConsts {
+    uint32_t rk0[10], rk1[10];   // Philox round keys: seed + r * Weyl constant
+    uint32_t n_items;            // warp items in the launch
+    uint32_t single_point;       // 1: one point, item i covers paths 32 i .. 32 i + 31
+    uint64_t budget_ns;          // device-time budget per warp (from its start), 0 = none
+};
+
+// Per-point constants, precomputed on the host in FP64 and rounded once.
+struct PointConsts {
+    // integrator (coordinate units of the model; see the host code)
+    float gdt;        // gamma dt                                 (inertial)
+    float fdt;        // force amplitude x dt in coordinate units
+    float wdt;        // coordinate advance per unit velocity per step (inertial)
+    float whdt;       // half of wdt                              (inertial)
+    float a_dt, F_dt; // drive amplitude and bias x dt in coordinate units
+    uint64_t phase_step;  // omega dt / 2 pi as a 0.64 fixed-point fraction
+    // noise
+    float xi_c;       // Gaussian increment scale (G sqrt(3 dt) or G sqrt(dt))
+    float aP_dt;      // Poisson bias a dt
+    float zeta_l2;    // zeta ln 2 (amplitude from log2)
+    float pois_cl2;   // ln 2 / (lambda dt)
+    float Fb_dt, mFa_dt;        // dichotomous increments F_b dt and -F_a dt
+    float mua_cl2, mub_cl2;     // ln 2 / (mu dt)
+    double inv_lambda, inv_mua, inv_mub, dt64;   // exact (FP64) waiting times
+    uint32_t d0_thresh;         // initial state F_b iff (w >> 8) < d0_thresh
+    uint32_t gauss_on;
+    // initial state
+    float x0_lo, x0_span, v0_lo, v0_span;
+    // counters
+    uint32_t c1_init, c1_gauss, c1_pois, c1_dich;   // (tag << 30) | point
+    // run
+    uint32_t n_tr, n_avg, n_paths, first_item;
+    double inv_window;  // 1 / (n_avg dt)
+    double period;      // spatial period L in x units
+    double coord_to_x;  // x = coordinate * coord_to_x (1 / 2 pi for washboards)
+};
+
+struct PathOutPtrs {
+    double* X_f;
+    float* v_f;
+    double* vbar;
+    uint32_t* jP;
+    uint32_t* jD;
+};
+
+// ---------------------------------------------------------------- Philox
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+
+// Philox4x32-10 (Salmon et al., SC'11) with precomputed round keys.
+__device__ __forceinline__ uint4 philox10(uint4 c, const LaunchConsts& K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ K.rk1[r], (uint32_t)p0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 stream(const LaunchConsts& K, uint32_t c1, uint32_t path, uint32_t idx)
+{
+    return philox10(make_uint4(idx, c1, path, 0u), K);
+}
+
+// SFU approximations (PTX cos.approx / lg2.approx, flush-to-zero: the
+// arguments here are never subnormal).
+__device__ __forceinline__ float cos_sfu(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_sfu(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// phi = (w >> 8) 2^-24 in [0,1) and u = 1 - phi in (0,1], both exact in FP32.
+__device__ __forceinline__ float phi24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(0x1000000u - (w >> 8)) * 0x1p-24f; }
+
+// Waiting steps floor(-ln(u) / (rate dt)) (Algorithms 3 and 4).  The fast
+// path uses the SFU log2 (absolute error about 2^-22 on u in (0, 1]); when
+// the quotient lies within a margin of an integer that is 2^6 times the
+// resulting error bound plus the rounding of the product, the decision is
+// taken again with the paper's expression in FP64, so the integer equals the
+// FP64 floor.
+__device__ __forceinline__ int32_t wait_steps(uint32_t w, float cl2, double inv_rate, double dt)
+{
+    const float u = u24(w);
+    float y = -lg2_sfu(u) * cl2;
+    y = fminf(y, 2.0e9f);
+    const float fl = floorf(y);
+    const float fr = y - fl;
+    const float m = (cl2 + y) * 0x1p-16f;
+    if (fr < m || fr > 1.0f - m) {
+        const double q = -inv_rate * log((double)u) / dt;
+        return (int32_t)fmin(floor(q), 2.0e9);
+    }
+    return (int32_t)fl;
+}
+
+// Drive a cos(omega t_n) + F at step n, times dt in coordinate units.
+__device__ __forceinline__ float drive_at(uint32_t n, const PointConsts& P)
+{
+    const uint64_t ph = (uint64_t)n * P.phase_step;       // fraction of a period, mod 1
+    const int32_t hi = (int32_t)(uint32_t)(ph >> 32);     // in [-1/2, 1/2) periods, Q0.32
+    const float two_r = (float)hi * 0x1p-31f;
+    return fmaf(P.a_dt, cospif(two_r), P.F_dt);
+}
+
+// ---------------------------------------------------------------- path state
+
+struct PathState {
+    float c;      // folded coordinate: 2 pi x in [-pi, pi) (washboards), x in [-1, 1) (PWL)
+    float v;      // velocity (inertial)
+    float kf;     // whole periods folded out of c (exact integer in FP32)
+    float c_i, kf_i;                // snapshot at t_i
+    float sv, sv2;                  // FP32 window partials of v and v^2
+    double svd, sv2d;               // FP64 window accumulators
+    int32_t sP; uint32_t jP; uint32_t pw2, pw3;              // Poisson (Algorithm 3)
+    int32_t sD; uint32_t jD; uint32_t dst; float gam;        // dichotomous (Algorithm 4)
+    uint32_t dw1, dw2, dw3;
+};
+
+template <int MODEL>
+__device__ __forceinline__ void fold(PathState& S)
+{
+    if (MODEL == kModelPWL) {
+        const float r = floorf((S.c + 1.0f) * 0.5f);     // c -> [-1, 1), period 2
+        S.c = fmaf(-2.0f, r, S.c);
+        S.kf += r;
+    } else {
+        const float r = rintf(S.c * 0.15915494309189535f); // c -> [-pi, pi]
+        S.c = fmaf(-6.2831853071795865f, r, S.c);
+        S.kf += r;
+    }
+}
+
+// -V'(coordinate) x dt in coordinate units.
+template <int MODEL>
+__device__ __forceinline__ float force_dt(float c, const PointConsts& P)
+{
+    if (MODEL == kModelPWL) {
+        // V' = +1 on [-1, 0), -1 on [0, 1) (mod 2): force -V0 V'
+        const float y = c - 2.0f * floorf((c + 1.0f) * 0.5f);
+        return y < 0.0f ? -P.fdt : P.fdt;
+    } else {
+        return -P.fdt * cos_sfu(c);
+    }
+}
+
+template <bool ACC>
+__device__ __forceinline__ void accumulate(PathState& S)
+{
+    if (ACC) {
+        S.sv += S.v;
+        S.sv2 = fmaf(S.v, S.v, S.sv2);
+    }
+}
+
+// One step of Algorithm 1.  dxi: Gaussian increment; jump: Poissonian plus
+// dichotomous increment (corrector only); d0 / d1: drive x dt at t_n, t_{n+1}.
+template <int MODEL, bool ACC>
+__device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, float dxi,
+                                        float jump, float d0, float d1)
+{
+    if (MODEL == kModelInertial) {
+        const float b1 = fmaf(-P.gdt, S.v, d0) + force_dt<MODEL>(S.c, P);   // F1_v dt
+        const float vxi = S.v + dxi;
+        float cb = fmaf(P.wdt, S.v, S.c);                                   // Euler x
+        float vb = vxi + b1;                                                // Euler v
+        const float b2 = fmaf(-P.gdt, vb, d1) + force_dt<MODEL>(cb, P);
+        const float ch = fmaf(P.whdt, S.v, S.c);
+        const float h1 = fmaf(0.5f, b1, vxi);
+        cb = fmaf(P.whdt, vb, ch);                                          // predictor x
+        vb = fmaf(0.5f, b2, h1);                                            // predictor v
+        const float b3 = fmaf(-P.gdt, vb, d1) + force_dt<MODEL>(cb, P);
+        S.c = fmaf(P.whdt, vb, ch);                                         // corrector x
+        S.v = fmaf(0.5f, b3, h1 + jump);                                    // corrector v
+        fold<MODEL>(S);
+        accumulate<ACC>(S);
+    } else {
+        const float b1 = d0 + force_dt<MODEL>(S.c, P);
+        const float cxi = S.c + dxi;
+        float cb = cxi + b1;                                                // Euler
+        const float b2 = d1 + force_dt<MODEL>(cb, P);
+        const float h1 = fmaf(0.5f, b1, cxi);
+        cb = fmaf(0.5f, b2, h1);                                            // predictor
+        const float b3 = d1 + force_dt<MODEL>(cb, P);
+        S.c = fmaf(0.5f, b3, h1 + jump);                                    // corrector
+        fold<MODEL>(S);
+    }
+}
+
+// Algorithm 3: Poissonian increment of this step (scaled to coordinate units).
+__device__ __forceinline__ float pois_step(PathState& S, const PointConsts& P,
+                                           const LaunchConsts& K, uint32_t path)
+{
+    float d = -P.aP_dt;
+    if (S.sP <= 0) {
+        S.jP += 1u;
+        uint32_t wa, wb;
+        if ((S.jP & 1u) == 0u) {
+            const uint4 w = stream(K, P.c1_pois, path, S.jP >> 1);
+            wa = w.x; wb = w.y; S.pw2 = w.z; S.pw3 = w.w;
+        } else {
+            wa = S.pw2; wb = S.pw3;
+        }
+        S.sP = wait_steps(wa, P.pois_cl2, P.inv_lambda, P.dt64);
+        d = fmaf(-P.zeta_l2, lg2_sfu(u24(wb)), d);
+    } else {
+        S.sP -= 1;
+    }
+    return d;
+}
+
+// Algorithm 4: dichotomous increment of this step (scaled to coordinate units).
+__device__ __forceinline__ float dich_step(PathState& S, const PointConsts& P,
+                                           const LaunchConsts& K, uint32_t path)
+{
+    if (S.sD <= 0) {
+        S.jD += 1u;
+        S.dst ^= 1u;
+        const uint32_t k = S.jD & 3u;
+        uint32_t w;
+        if (k == 0u) {
+            const uint4 b = stream(K, P.c1_dich, path, S.jD >> 2);
+            w = b.x; S.dw1 = b.y; S.dw2 = b.z; S.dw3 = b.w;
+        } else {
+            w = k == 1u ? S.dw1 : (k == 2u ? S.dw2 : S.dw3);
+        }
+        S.gam = S.dst ? P.Fb_dt : P.mFa_dt;
+        S.sD = S.dst ? wait_steps(w, P.mub_cl2, P.inv_mub, P.dt64)
+                     : wait_steps(w, P.mua_cl2, P.inv_mua, P.dt64);
+    } else {
+        S.sD -= 1;
+    }
+    return S.gam;
+}
+
+// Gaussian increment for step n from the word of its group (Algorithm 2 / Eq. 25
+// three-point law, or Box-Muller for the Gaussian variant).
+template <int GAUSS>
+__device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const PointConsts& P)
+{
+    if (GAUSS == kGauss3Point) {
+        const uint32_t r = k == 0u ? w.x : (k == 1u ? w.y : (k == 2u ? w.z : w.w));
+        float d = r <= 1431655765u ? P.xi_c : 0.0f;     // phi <= 1/3
+        d = r <= 715827882u ? -P.xi_c : d;              // phi <= 1/6
+        return d;
+    } else {
+        const uint32_t wa = k < 2u ? w.x : w.z;
+        const uint32_t wb = k < 2u ? w.y : w.w;
+        const float R = sqrtf(-2.0f * __logf(u24(wa)));
+        // angle 2 pi phi - pi in [-pi, pi): cos/sin change sign
+        const float T = fmaf(6.2831853071795865f, phi24(wb), -3.14159265358979f);
+        float s, c;
+        __sincosf(T, &s, &c);
+        return -P.xi_c * R * ((k & 1u) ? s : c);
+    }
+}
+
+// Steps n in [n_begin, n_end) one at a time (phase edges that are not whole
+// 32-step chunks).
+template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
+__device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                             uint32_t path, uint32_t n, uint32_t n_end)
+{
+    for (; n < n_end; ++n) {
+        float dxi = 0.0f;
+        if (P.gauss_on) {
+            const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
+            dxi = gauss_inc<GAUSS>(w, n & 3u, P);
+        }
+        float jump = 0.0f;
+        if (POIS) jump += pois_step(S, P, K, path);
+        if (DICH) jump += dich_step(S, P, K, path);
+        pc_step<MODEL, ACC>(S, P, dxi, jump, drive_at(n, P), drive_at(n + 1u, P));
+    }
+}
+
+// Steps n in [n_begin, n_end): aligned 32-step chunks share one drive
+// evaluation per lane (lane l computes the drive at n0 + 1 + l; each step
+// takes its value with a warp shuffle), the Gaussian stream is drawn one
+// Philox call per 4 steps.  All 32 lanes of the warp must call this together.
+template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
+__device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                          uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
+{
+    uint32_t head = n;                                   // first chunk boundary
+    if ((n & 31u) != 0u) head = min(n_end, (n + 31u) & ~31u);
+    if (head > n) {
+        single_steps<MODEL, POIS, DICH, GAUSS, ACC>(S, P, K, path, n, head);
+        n = head;
+    }
+    if (n + 32u <= n_end) {
+        float dcur = drive_at(n, P);
+        for (; n + 32u <= n_end; n += 32u) {
+            const float dch = drive_at(n + 1u + lane, P);
+#pragma unroll 1
+            for (uint32_t g = 0; g < 8u; ++g) {
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (P.gauss_on) w = stream(K, P.c1_gauss, path, (n >> 2) + g);
+#pragma unroll
+                for (uint32_t k = 0; k < 4u; ++k) {
+                    const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
+                    const float dxi = P.gauss_on ? gauss_inc<GAUSS>(w, k, P) : 0.0f;
+                    float jump = 0.0f;
+                    if (POIS) jump += pois_step(S, P, K, path);
+                    if (DICH) jump += dich_step(S, P, K, path);
+                    pc_step<MODEL, ACC>(S, P, dxi, jump, dcur, dnext);
+                    dcur = dnext;
+                }
+            }
+            if (ACC) {
+                S.svd += (double)S.sv;
+                S.sv2d += (double)S.sv2;
+                S.sv = 0.0f;
+                S.sv2 = 0.0f;
+            }
+        }
+    }
+    if (n < n_end) single_steps<MODEL, POIS, DICH, GAUSS, ACC>(S, P, K, path, n, n_end);
+}
+
+template <int MODEL, bool POIS, bool DICH>
+__device__ __forceinline__ void init_path(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                          uint32_t path)
+{
+    const uint4 w = stream(K, P.c1_init, path, 0u);
+    const float x0 = fmaf(P.x0_span, phi24(w.x), P.x0_lo);
+    S.c = MODEL == kModelPWL ? x0 : x0 * 6.2831853071795865f;
+    S.v = MODEL == kModelInertial ? fmaf(P.v0_span, phi24(w.y), P.v0_lo) : 0.0f;
+    S.kf = 0.0f;
+    fold<MODEL>(S);
+    S.sv = S.sv2 = 0.0f;
+    S.svd = S.sv2d = 0.0;
+    S.sP = 0; S.jP = 0u; S.pw2 = S.pw3 = 0u;
+    S.sD = 0; S.jD = 0u; S.dst = 0u; S.gam = 0.0f; S.dw1 = S.dw2 = S.dw3 = 0u;
+    if (POIS) {
+        const uint4 e = stream(K, P.c1_pois, path, 0u);        // event 0: countdown only
+        S.sP = wait_steps(e.x, P.pois_cl2, P.inv_lambda, P.dt64);
+        S.pw2 = e.z; S.pw3 = e.w;
+    }
+    if (DICH) {
+        S.dst = (w.z >> 8) < P.d0_thresh ? 1u : 0u;             // stationary start
+        S.gam = S.dst ? P.Fb_dt : P.mFa_dt;
+        const uint4 e = stream(K, P.c1_dich, path, 0u);
+        S.sD = S.dst ? wait_steps(e.x, P.mub_cl2, P.inv_mub, P.dt64)
+                     : wait_steps(e.x, P.mua_cl2, P.inv_mua, P.dt64);
+        S.dw1 = e.y; S.dw2 = e.z; S.dw3 = e.w;
+    }
+}
+
+struct PathResult {
+    double X_f, vbar, sum_v, sum_v2;
+    float v_f;
+    uint32_t jP, jD;
+};
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS>
+__device__ __forceinline__ void simulate_path(const PointConsts& P, const LaunchConsts& K,
+                                              uint32_t path, uint32_t lane, PathResult& R)
+{
+    PathState S;
+    init_path<MODEL, POIS, DICH>(S, P, K, path);
+    run_steps<MODEL, POIS, DICH, GAUSS, false>(S, P, K, path, lane, 0u, P.n_tr);
+    S.c_i = S.c;
+    S.kf_i = S.kf;
+    run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane, P.n_tr,
+                                                                 P.n_tr + P.n_avg);
+    const double dX = ((double)S.kf - (double)S.kf_i) * P.period
+                    + ((double)S.c - (double)S.c_i) * P.coord_to_x;
+    R.X_f = (double)S.kf * P.period + (double)S.c * P.coord_to_x;
+    R.vbar = dX * P.inv_window;
+    R.sum_v = S.svd + (double)S.sv;
+    R.sum_v2 = S.sv2d + (double)S.sv2;
+    R.v_f = S.v;
+    R.jP = S.jP;
+    R.jD = S.jD;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Pull the next warp item (lane 0 increments the counter); UINT32_MAX = done.
+// With a budget, a warp that has run longer than it since t0 takes no further
+// item and marks the launch as timed out (the host reads the status word).
+__device__ __forceinline__ uint32_t next_item(uint32_t* counter, int32_t* status,
+                                              const LaunchConsts& K, uint32_t lane, uint64_t t0)
+{
+    uint32_t item = 0u;
+    if (lane == 0u) {
+        if (K.budget_ns != 0ull && globaltimer_ns() - t0 > K.budget_ns) {
+            atomicExch(status, kStatusTimedOut);
+            item = 0xffffffffu;
+        } else {
+            item = atomicAdd(counter, 1u);
+        }
+    }
+    item = __shfl_sync(0xffffffffu, item, 0);
+    return item < K.n_items ? item : 0xffffffffu;
+}
+
+// Write one item's FP64 partial sums {paths, sum vbar, sum vbar^2, sum v, sum v^2}.
+__device__ __forceinline__ void store_partial(double* partials, uint32_t item, uint32_t lane,
+                                              bool valid, const PathResult& R)
+{
+    const double n = warp_sum(valid ? 1.0 : 0.0);
+    const double s1 = warp_sum(valid ? R.vbar : 0.0);
+    const double s2 = warp_sum(valid ? R.vbar * R.vbar : 0.0);
+    const double s3 = warp_sum(valid ? R.sum_v : 0.0);
+    const double s4 = warp_sum(valid ? R.sum_v2 : 0.0);
+    if (lane == 0u) {
+        double* o = partials + 5ull * item;
+        o[0] = n; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = s4;
+    }
+}
+
+__device__ __forceinline__ void store_path(const PathOutPtrs& po, uint32_t path, const PathResult& R)
+{
+    if (po.X_f) po.X_f[path] = R.X_f;
+    if (po.v_f) po.v_f[path] = R.v_f;
+    if (po.vbar) po.vbar[path] = R.vbar;
+    if (po.jP) po.jP[path] = R.jP;
+    if (po.jD) po.jD[path] = R.jD;
+}
+
+}  // namespace sde

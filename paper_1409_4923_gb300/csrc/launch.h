@@ -1,0 +1,41 @@
+// launch.h -- host-side launchers of the engine's kernels (internal header).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace sde {
+
+struct Workspace {
+    uint32_t* counter;   // work-item counter (must start at 0)
+    int32_t* status;     // kStatusOk / kStatusTimedOut (must start at 0)
+    double* partials;    // 5 doubles per warp item
+};
+
+// Launch the single-point path kernel for (model, poisson, dichotomous, gauss).
+// grid_blocks == 0 picks a persistent grid from the occupancy calculator.
+cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+                         const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
+                         int block_threads, int grid_blocks, int sm_count, cudaStream_t st);
+
+// Inertial-washboard scan kernel over an item table of (point, first path).
+cudaError_t launch_scan(bool pois, bool dich, const PointConsts* pts_dev, const uint2* items_dev,
+                        const LaunchConsts& K, const Workspace& ws, int block_threads,
+                        int grid_blocks, int sm_count, cudaStream_t st);
+
+// Fixed-order FP64 fold of item partials: ranges[p] = (first item, item count),
+// out5[5 p .. 5 p + 4] receives the point's five sums.
+cudaError_t launch_fold(const double* partials, const uint2* ranges, uint32_t npts,
+                        double* out5, cudaStream_t st);
+
+// Warp items of 32 doubles -> partials {n, sum, sum of squares, 0, 0}.
+cudaError_t launch_reduce_items(const double* vals, uint64_t n, double* partials, cudaStream_t st);
+
+cudaError_t launch_philox(const uint4* ctr, uint64_t n, const LaunchConsts& K, uint4* out,
+                          cudaStream_t st);
+
+// Occupancy-derived resident blocks per SM for the kernel a launch would use.
+int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int block_threads);
+
+}  // namespace sde

@@ -1,0 +1,93 @@
+// point_kernels.cuh -- the single-point path kernel and its instantiation table.
+#pragma once
+#include "launch.h"
+
+namespace sde {
+
+// Persistent warp-item kernel for one parameter point: each warp pulls
+// 32-path items, integrates its lane's path for n_transient + n_avg steps
+// and writes the item's FP64 partial sums (and, optionally, per-path results).
+template <int MODEL, bool POIS, bool DICH, int GAUSS>
+__global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ PointConsts P,
+                                                    const __grid_constant__ LaunchConsts K,
+                                                    uint32_t* __restrict__ counter,
+                                                    int32_t* __restrict__ status,
+                                                    double* __restrict__ partials,
+                                                    const PathOutPtrs po)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t t0 = K.budget_ns ? globaltimer_ns() : 0ull;
+    for (;;) {
+        const uint32_t item = next_item(counter, status, K, lane, t0);
+        if (item == 0xffffffffu) break;
+        const uint32_t path = item * 32u + lane;
+        const bool valid = path < P.n_paths;
+        PathResult R;
+        simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, path, lane, R);
+        if (valid) store_path(po, path, R);
+        store_partial(partials, item, lane, valid, R);
+    }
+}
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS>
+cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Workspace& ws,
+                           const PathOutPtrs& po, int block_threads, int grid_blocks,
+                           int sm_count, cudaStream_t st)
+{
+    auto kern = point_kernel<MODEL, POIS, DICH, GAUSS>;
+    if (grid_blocks <= 0) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_threads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        const uint64_t warps = (uint64_t)K.n_items;
+        const uint64_t need = (warps * 32ull + block_threads - 1) / block_threads;
+        uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count;
+        grid_blocks = (int)(need < cap ? need : cap);
+        if (grid_blocks < 1) grid_blocks = 1;
+    }
+    kern<<<grid_blocks, block_threads, 0, st>>>(P, K, ws.counter, ws.status, ws.partials, po);
+    return cudaGetLastError();
+}
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS>
+int blocks_per_sm_t(int block_threads)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, point_kernel<MODEL, POIS, DICH, GAUSS>,
+                                                  block_threads, 0);
+    return per_sm;
+}
+
+// Dispatch over the noise switches for one model (instantiated per model in
+// its own translation unit).
+template <int MODEL>
+cudaError_t launch_point_model(bool pois, bool dich, int gauss, const PointConsts& P,
+                               const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
+                               int bt, int gb, int sm, cudaStream_t st)
+{
+#define SDE_CASE(PO, DI, GA) \
+    if (pois == PO && dich == DI && gauss == GA) \
+        return launch_point_t<MODEL, PO, DI, GA>(P, K, ws, po, bt, gb, sm, st);
+    SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
+    SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
+    SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
+    SDE_CASE(false, true, kGaussNormal) SDE_CASE(true, true, kGaussNormal)
+#undef SDE_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int MODEL>
+int blocks_per_sm_model(bool pois, bool dich, int gauss, int bt)
+{
+#define SDE_CASE(PO, DI, GA) \
+    if (pois == PO && dich == DI && gauss == GA) return blocks_per_sm_t<MODEL, PO, DI, GA>(bt);
+    SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
+    SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
+    SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
+    SDE_CASE(false, true, kGaussNormal) SDE_CASE(true, true, kGaussNormal)
+#undef SDE_CASE
+    return 0;
+}
+
+}  // namespace sde
