@@ -41,7 +41,7 @@ int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int bt)
 // Persistent scan over (point, 32-path tile) items of the inertial washboard
 // (Sec. 5: many parameter values in one kernel call).  Items are ordered
 // longest first on the host; each warp pulls the next one from the counter.
-template <bool POIS, bool DICH>
+template <bool POIS, bool DICH, int GAUSS>
 __global__ void __launch_bounds__(128) scan_kernel(const PointConsts* __restrict__ pts,
                                                    const uint2* __restrict__ items,
                                                    const __grid_constant__ LaunchConsts K,
@@ -59,16 +59,16 @@ __global__ void __launch_bounds__(128) scan_kernel(const PointConsts* __restrict
         const uint32_t path = it.y + lane;
         const bool valid = path < P.n_paths;
         PathResult R;
-        simulate_path<kModelInertial, POIS, DICH, kGauss3Point>(P, K, path, lane, R);
+        simulate_path<kModelInertial, POIS, DICH, GAUSS>(P, K, path, lane, R);
         store_partial(partials, item, lane, valid, R);
     }
 }
 
-template <bool POIS, bool DICH>
+template <bool POIS, bool DICH, int GAUSS>
 static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, const LaunchConsts& K,
                                  const Workspace& ws, int bt, int gb, int sm, cudaStream_t st)
 {
-    auto kern = scan_kernel<POIS, DICH>;
+    auto kern = scan_kernel<POIS, DICH, GAUSS>;
     if (gb <= 0) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bt, 0);
@@ -83,14 +83,18 @@ static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(bool pois, bool dich, const PointConsts* pts, const uint2* items,
+cudaError_t launch_scan(bool pois, bool dich, int gauss, const PointConsts* pts, const uint2* items,
                         const LaunchConsts& K, const Workspace& ws, int bt, int gb, int sm,
                         cudaStream_t st)
 {
-    if (pois && dich) return launch_scan_t<true, true>(pts, items, K, ws, bt, gb, sm, st);
-    if (pois) return launch_scan_t<true, false>(pts, items, K, ws, bt, gb, sm, st);
-    if (dich) return launch_scan_t<false, true>(pts, items, K, ws, bt, gb, sm, st);
-    return launch_scan_t<false, false>(pts, items, K, ws, bt, gb, sm, st);
+#define SDE_SCAN(PO, DI, GA) \
+    if (pois == PO && dich == DI && gauss == GA) \
+        return launch_scan_t<PO, DI, GA>(pts, items, K, ws, bt, gb, sm, st);
+    SDE_SCAN(true, true, kGauss3Point) SDE_SCAN(true, false, kGauss3Point)
+    SDE_SCAN(false, true, kGauss3Point) SDE_SCAN(false, false, kGauss3Point)
+    SDE_SCAN(true, true, 0) SDE_SCAN(true, false, 0) SDE_SCAN(false, true, 0) SDE_SCAN(false, false, 0)
+#undef SDE_SCAN
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------- FP64 fold

@@ -13,7 +13,7 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/sde.h"
+#include "sde.h"
 #include "launch.h"
 
 using namespace sde;
@@ -21,7 +21,7 @@ using namespace sde;
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr uint32_t kMaxSteps = 0xFFFFFF00u;   // n_transient + n_avg, keeps 32-bit step indices
+constexpr uint32_t kMaxSteps = 0x7FFFFF00u;   // n_transient + n_avg: event steps stay below 2^32
 
 struct ScanGraph {
     cudaGraph_t graph = nullptr;
@@ -101,11 +101,16 @@ static int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, ui
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDE_EINVAL, "dt must be finite and > 0");
     if (n_avg < 1) return fail(c, SDE_EINVAL, "n_avg must be >= 1");
     if (n_tr > kMaxSteps || n_avg > kMaxSteps || n_tr + n_avg > kMaxSteps)
-        return fail(c, SDE_EINVAL, "n_transient + n_avg must be < 2^32 - 256");
+        return fail(c, SDE_EINVAL, "n_transient + n_avg must be < 2^31 - 256");
     return SDE_OK;
 }
 
-static int gauss_kind(uint32_t flags) { return (flags & SDE_GAUSS_NORMAL) ? kGaussNormal : kGauss3Point; }
+// Gaussian kernel variant: none (flag off or zero intensity), three-point, Gaussian.
+static int gauss_kind(const sde_params& p)
+{
+    if (!(p.noise_flags & SDE_NOISE_GAUSS) || !(p.Q > 0.0)) return 0;
+    return (p.noise_flags & SDE_GAUSS_NORMAL) ? kGaussNormal : kGauss3Point;
+}
 
 // Kernel constants of one point, from the FP64 parameters.  Coordinates:
 // washboards integrate c = 2 pi x (so the SFU cosine takes c directly), the
@@ -135,19 +140,18 @@ static int make_point(sde_ctx* c, sde_model model, const sde_params& p, double d
     P.phase_step = fx >= 18446744073709551615.0 ? 0ull : (uint64_t)fx;
 
     const double G = inertial ? std::sqrt(2.0 * p.gamma * p.Q) : std::sqrt(2.0 * p.Q);
-    P.gauss_on = (f & SDE_NOISE_GAUSS) && G > 0.0 ? 1u : 0u;
     P.xi_c = (float)(ns * G * ((f & SDE_GAUSS_NORMAL) ? std::sqrt(dt) : std::sqrt(3.0 * dt)));
     if (f & SDE_NOISE_POISSON) {
         const double aP = (f & SDE_POIS_COMPENSATED) ? p.zeta * (-std::expm1(-p.lambda * dt)) / dt
                                                      : p.lambda * p.zeta;
-        if (p.lambda * dt < 1e-8) return fail(c, SDE_EINVAL, "lambda dt must be >= 1e-8");
+        if (p.lambda * dt < 2e-8) return fail(c, SDE_EINVAL, "lambda dt must be >= 2e-8");
         P.aP_dt = (float)(ns * aP * dt);
         P.zeta_l2 = (float)(ns * p.zeta * M_LN2);
         P.pois_cl2 = (float)(M_LN2 / (p.lambda * dt));
         P.inv_lambda = 1.0 / p.lambda;
     }
     if (f & SDE_NOISE_DICHOT) {
-        if (p.mua * dt < 1e-8 || p.mub * dt < 1e-8) return fail(c, SDE_EINVAL, "mu dt must be >= 1e-8");
+        if (p.mua * dt < 2e-8 || p.mub * dt < 2e-8) return fail(c, SDE_EINVAL, "mu dt must be >= 2e-8");
         P.Fb_dt = (float)(ns * p.Fb * dt);
         P.mFa_dt = (float)(-ns * p.Fa * dt);
         P.mua_cl2 = (float)(M_LN2 / (p.mua * dt));
@@ -334,7 +338,7 @@ int sde_occupancy(sde_ctx* c, int block_threads, int* blocks_per_sm, int* sm_cou
     if (!c || !blocks_per_sm || !sm_count) return SDE_EINVAL;
     const uint32_t f = c->p.noise_flags;
     *blocks_per_sm = point_blocks_per_sm((int)c->model, (f & SDE_NOISE_POISSON) != 0,
-                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(f), block_threads);
+                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p), block_threads);
     *sm_count = c->sm_count;
     return SDE_OK;
 }
@@ -364,7 +368,7 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
     const LaunchConsts K = make_launch(c->seed, (uint32_t)items, 0);
     const uint32_t f = c->p.noise_flags;
     SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
-                             gauss_kind(f), P, K, ws, po, c->block_threads, c->grid_blocks,
+                             gauss_kind(c->p), P, K, ws, po, c->block_threads, c->grid_blocks,
                              c->sm_count, c->stream));
     SDE_CUDA(c, launch_fold(ws.partials, ranges, 1, out5, c->stream));
     SDE_CUDA(c, cudaMemcpyAsync(c->host, out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -461,7 +465,8 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             if (capture) SDE_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaMemsetAsync(base, 0, 8, c->stream);
             if (e == cudaSuccess)
-                e = launch_scan((flags & SDE_NOISE_POISSON) != 0, (flags & SDE_NOISE_DICHOT) != 0, d_pts,
+                e = launch_scan((flags & SDE_NOISE_POISSON) != 0, (flags & SDE_NOISE_DICHOT) != 0,
+                                (flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0, d_pts,
                                 d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream);
             if (e == cudaSuccess) e = launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream);
             if (e == cudaSuccess)
@@ -493,7 +498,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             SDE_CUDA(c, cudaMemsetAsync(base, 0, 4, c->stream));
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (flags & SDE_NOISE_POISSON) != 0,
-                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(flags), P[i], K, wsi,
+                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(pts[i].p), P[i], K, wsi,
                                      po, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
         SDE_CUDA(c, launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream));

@@ -49,7 +49,7 @@ struct PointConsts {
     float mua_cl2, mub_cl2;     // ln 2 / (mu dt)
     double inv_lambda, inv_mua, inv_mub, dt64;   // exact (FP64) waiting times
     uint32_t d0_thresh;         // initial state F_b iff (w >> 8) < d0_thresh
-    uint32_t gauss_on;
+    uint32_t gauss_pad;
     // initial state
     float x0_lo, x0_span, v0_lo, v0_span;
     // counters
@@ -122,13 +122,13 @@ __device__ __forceinline__ int32_t wait_steps(uint32_t w, float cl2, double inv_
 {
     const float u = u24(w);
     float y = -lg2_sfu(u) * cl2;
-    y = fminf(y, 2.0e9f);
+    y = fminf(y, 1.0e9f);
     const float fl = floorf(y);
     const float fr = y - fl;
     const float m = (cl2 + y) * 0x1p-16f;
     if (fr < m || fr > 1.0f - m) {
         const double q = -inv_rate * log((double)u) / dt;
-        return (int32_t)fmin(floor(q), 2.0e9);
+        return (int32_t)fmin(floor(q), 1.0e9);
     }
     return (int32_t)fl;
 }
@@ -144,16 +144,19 @@ __device__ __forceinline__ float drive_at(uint32_t n, const PointConsts& P)
 
 // ---------------------------------------------------------------- path state
 
+// A jump process is held as its next event: the absolute step e at which it
+// happens, its index J (events are numbered 1, 2, ...; index 0 is the initial
+// countdown of Algorithms 3 and 4) and the cached words of the Philox block
+// that serves the following events.  Algorithm 3's countdown s is e - n.
 struct PathState {
-    float c;      // folded coordinate: 2 pi x in [-pi, pi) (washboards), x in [-1, 1) (PWL)
+    float c;      // folded coordinate: 2 pi x near [-pi, pi) (washboards), x in [-1, 1) (PWL)
     float v;      // velocity (inertial)
     float kf;     // whole periods folded out of c (exact integer in FP32)
     float c_i, kf_i;                // snapshot at t_i
     float sv, sv2;                  // FP32 window partials of v and v^2
     double svd, sv2d;               // FP64 window accumulators
-    int32_t sP; uint32_t jP; uint32_t pw2, pw3;              // Poisson (Algorithm 3)
-    int32_t sD; uint32_t jD; uint32_t dst; float gam;        // dichotomous (Algorithm 4)
-    uint32_t dw1, dw2, dw3;
+    uint32_t eP, JP, pw2, pw3;                  // Poisson (Algorithm 3)
+    uint32_t eD, JD, dst, dw1, dw2, dw3;        // dichotomous (Algorithm 4), dst 1 = F_b
 };
 
 template <int MODEL>
@@ -169,6 +172,11 @@ __device__ __forceinline__ void fold(PathState& S)
         S.kf += r;
     }
 }
+
+// The inertial coordinate moves by at most 2 pi |v| dt per step, so folding it
+// once per 4 steps keeps it inside (-4, 4), the same FP32 binade as [-pi, pi];
+// the overdamped coordinates are folded every step.
+template <int MODEL> struct FoldPerStep { static constexpr bool value = MODEL != kModelInertial; };
 
 // -V'(coordinate) x dt in coordinate units.
 template <int MODEL>
@@ -194,7 +202,7 @@ __device__ __forceinline__ void accumulate(PathState& S)
 
 // One step of Algorithm 1.  dxi: Gaussian increment; jump: Poissonian plus
 // dichotomous increment (corrector only); d0 / d1: drive x dt at t_n, t_{n+1}.
-template <int MODEL, bool ACC>
+template <int MODEL, bool ACC, bool FOLD>
 __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, float dxi,
                                         float jump, float d0, float d1)
 {
@@ -211,7 +219,6 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         const float b3 = fmaf(-P.gdt, vb, d1) + force_dt<MODEL>(cb, P);
         S.c = fmaf(P.whdt, vb, ch);                                         // corrector x
         S.v = fmaf(0.5f, b3, h1 + jump);                                    // corrector v
-        fold<MODEL>(S);
         accumulate<ACC>(S);
     } else {
         const float b1 = d0 + force_dt<MODEL>(S.c, P);
@@ -222,58 +229,109 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         cb = fmaf(0.5f, b2, h1);                                            // predictor
         const float b3 = d1 + force_dt<MODEL>(cb, P);
         S.c = fmaf(0.5f, b3, h1 + jump);                                    // corrector
-        fold<MODEL>(S);
     }
+    if (FOLD) fold<MODEL>(S);
 }
 
-// Algorithm 3: Poissonian increment of this step (scaled to coordinate units).
-__device__ __forceinline__ float pois_step(PathState& S, const PointConsts& P,
+// Algorithm 3 at event JP (step eP): the step's Poissonian increment z - a dt
+// (scaled to coordinate units) and the step of the next event.
+__device__ __forceinline__ float pois_event(PathState& S, const PointConsts& P,
+                                            const LaunchConsts& K, uint32_t path)
+{
+    uint32_t wa, wb;
+    if ((S.JP & 1u) == 0u) {
+        const uint4 w = stream(K, P.c1_pois, path, S.JP >> 1);
+        wa = w.x; wb = w.y; S.pw2 = w.z; S.pw3 = w.w;
+    } else {
+        wa = S.pw2; wb = S.pw3;
+    }
+    S.eP += (uint32_t)wait_steps(wa, P.pois_cl2, P.inv_lambda, P.dt64) + 1u;
+    S.JP += 1u;
+    return fmaf(-P.zeta_l2, lg2_sfu(u24(wb)), -P.aP_dt);
+}
+
+// Algorithm 4 at flip JD (step eD): the new state and the step of the next flip.
+__device__ __forceinline__ void dich_event(PathState& S, const PointConsts& P,
                                            const LaunchConsts& K, uint32_t path)
 {
-    float d = -P.aP_dt;
-    if (S.sP <= 0) {
-        S.jP += 1u;
-        uint32_t wa, wb;
-        if ((S.jP & 1u) == 0u) {
-            const uint4 w = stream(K, P.c1_pois, path, S.jP >> 1);
-            wa = w.x; wb = w.y; S.pw2 = w.z; S.pw3 = w.w;
-        } else {
-            wa = S.pw2; wb = S.pw3;
-        }
-        S.sP = wait_steps(wa, P.pois_cl2, P.inv_lambda, P.dt64);
-        d = fmaf(-P.zeta_l2, lg2_sfu(u24(wb)), d);
+    S.dst ^= 1u;
+    const uint32_t k = S.JD & 3u;
+    uint32_t w;
+    if (k == 0u) {
+        const uint4 b = stream(K, P.c1_dich, path, S.JD >> 2);
+        w = b.x; S.dw1 = b.y; S.dw2 = b.z; S.dw3 = b.w;
     } else {
-        S.sP -= 1;
+        w = k == 1u ? S.dw1 : (k == 2u ? S.dw2 : S.dw3);
     }
-    return d;
+    const float cl2 = S.dst ? P.mub_cl2 : P.mua_cl2;
+    const double inv_rate = S.dst ? P.inv_mub : P.inv_mua;
+    S.eD += (uint32_t)wait_steps(w, cl2, inv_rate, P.dt64) + 1u;
+    S.JD += 1u;
 }
 
-// Algorithm 4: dichotomous increment of this step (scaled to coordinate units).
-__device__ __forceinline__ float dich_step(PathState& S, const PointConsts& P,
-                                           const LaunchConsts& K, uint32_t path)
+// Jump increment of step n with the events drawn as they happen.
+template <bool POIS, bool DICH>
+__device__ __forceinline__ float jump_inline(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                             uint32_t path, uint32_t n)
 {
-    if (S.sD <= 0) {
-        S.jD += 1u;
-        S.dst ^= 1u;
-        const uint32_t k = S.jD & 3u;
-        uint32_t w;
-        if (k == 0u) {
-            const uint4 b = stream(K, P.c1_dich, path, S.jD >> 2);
-            w = b.x; S.dw1 = b.y; S.dw2 = b.z; S.dw3 = b.w;
-        } else {
-            w = k == 1u ? S.dw1 : (k == 2u ? S.dw2 : S.dw3);
-        }
-        S.gam = S.dst ? P.Fb_dt : P.mFa_dt;
-        S.sD = S.dst ? wait_steps(w, P.mub_cl2, P.inv_mub, P.dt64)
-                     : wait_steps(w, P.mua_cl2, P.inv_mua, P.dt64);
-    } else {
-        S.sD -= 1;
+    float j = 0.0f;
+    if (POIS) {
+        j = -P.aP_dt;
+        if (n == S.eP) j = pois_event(S, P, K, path);
     }
-    return S.gam;
+    if (DICH) {
+        if (n == S.eD) dich_event(S, P, K, path);
+        j += S.dst ? P.Fb_dt : P.mFa_dt;
+    }
+    return j;
 }
 
-// Gaussian increment for step n from the word of its group (Algorithm 2 / Eq. 25
-// three-point law, or Box-Muller for the Gaussian variant).
+// Events of the chunk [n0, n0 + 32), drawn before it is integrated so that
+// the warp draws them together instead of one divergent branch per step.
+// Bit i of pm marks a Poisson kick at step n0 + i, whose increments are
+// queued in kick order in z0, z1, z2; bit i of dm is the dichotomous state at
+// step n0 + i.  Returns false (and restores the Poisson state) when some lane
+// of the warp has more than three kicks in the chunk: the warp then takes the
+// Poisson events of this chunk inline.  All 32 lanes must call this together.
+template <bool POIS, bool DICH>
+__device__ __forceinline__ bool chunk_events(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                             uint32_t path, uint32_t n0, uint32_t& pm, float& z0,
+                                             float& z1, float& z2, uint32_t& dm)
+{
+    bool fits = true;
+    pm = 0u;
+    z0 = z1 = z2 = 0.0f;
+    dm = 0u;
+    if (POIS) {
+        const uint32_t e_save = S.eP, J_save = S.JP, w2_save = S.pw2, w3_save = S.pw3;
+        uint32_t cnt = 0u;
+        while (S.eP < n0 + 32u && cnt < 4u) {
+            const uint32_t off = S.eP - n0;
+            const float z = pois_event(S, P, K, path);
+            pm |= 1u << off;
+            z0 = cnt == 0u ? z : z0;
+            z1 = cnt == 1u ? z : z1;
+            z2 = cnt == 2u ? z : z2;
+            ++cnt;
+        }
+        if (__any_sync(0xffffffffu, cnt > 3u)) {
+            S.eP = e_save; S.JP = J_save; S.pw2 = w2_save; S.pw3 = w3_save;
+            fits = false;
+        }
+    }
+    if (DICH) {
+        dm = S.dst ? 0xffffffffu : 0u;
+        while (S.eD < n0 + 32u) {
+            const uint32_t off = S.eD - n0;
+            dich_event(S, P, K, path);
+            dm ^= 0xffffffffu << off;
+        }
+    }
+    return fits;
+}
+
+// Gaussian increment for step 4 i + k from the word of its group (Algorithm 2 /
+// Eq. 25 three-point law, or Box-Muller for the Gaussian variant).
 template <int GAUSS>
 __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const PointConsts& P)
 {
@@ -282,7 +340,7 @@ __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const Poi
         float d = r <= 1431655765u ? P.xi_c : 0.0f;     // phi <= 1/3
         d = r <= 715827882u ? -P.xi_c : d;              // phi <= 1/6
         return d;
-    } else {
+    } else if (GAUSS == kGaussNormal) {
         const uint32_t wa = k < 2u ? w.x : w.z;
         const uint32_t wb = k < 2u ? w.y : w.w;
         const float R = sqrtf(-2.0f * __logf(u24(wa)));
@@ -291,10 +349,12 @@ __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const Poi
         float s, c;
         __sincosf(T, &s, &c);
         return -P.xi_c * R * ((k & 1u) ? s : c);
+    } else {
+        return 0.0f;
     }
 }
 
-// Steps n in [n_begin, n_end) one at a time (phase edges that are not whole
+// Steps n in [n, n_end) one at a time (phase edges that are not whole
 // 32-step chunks).
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
@@ -302,21 +362,56 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 {
     for (; n < n_end; ++n) {
         float dxi = 0.0f;
-        if (P.gauss_on) {
+        if (GAUSS != 0) {
             const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
             dxi = gauss_inc<GAUSS>(w, n & 3u, P);
         }
-        float jump = 0.0f;
-        if (POIS) jump += pois_step(S, P, K, path);
-        if (DICH) jump += dich_step(S, P, K, path);
-        pc_step<MODEL, ACC>(S, P, dxi, jump, drive_at(n, P), drive_at(n + 1u, P));
+        const float jump = jump_inline<POIS, DICH>(S, P, K, path, n);
+        pc_step<MODEL, ACC, true>(S, P, dxi, jump, drive_at(n, P), drive_at(n + 1u, P));
     }
 }
 
-// Steps n in [n_begin, n_end): aligned 32-step chunks share one drive
-// evaluation per lane (lane l computes the drive at n0 + 1 + l; each step
-// takes its value with a warp shuffle), the Gaussian stream is drawn one
-// Philox call per 4 steps.  All 32 lanes of the warp must call this together.
+// One 32-step chunk from n0: 8 groups of 4 steps, one Philox call per group
+// for the Gaussian words, the drive of step n0 + 1 + l in lane l (shuffled to
+// every lane per step), jump events from the chunk masks (FAST) or inline.
+template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST>
+__device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                            uint32_t path, uint32_t n0, float dch, float& dcur,
+                                            uint32_t pm, float z0, float z1, float z2, uint32_t dm)
+{
+#pragma unroll 1
+    for (uint32_t g = 0; g < 8u; ++g) {
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (GAUSS != 0) w = stream(K, P.c1_gauss, path, (n0 >> 2) + g);
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+            const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
+            const float dxi = gauss_inc<GAUSS>(w, k, P);
+            float jump = 0.0f;
+            if (POIS) {
+                if (FAST) {
+                    const bool kick = (pm & (1u << k)) != 0u;
+                    jump = kick ? z0 : -P.aP_dt;
+                    z0 = kick ? z1 : z0;
+                    z1 = kick ? z2 : z1;
+                } else {
+                    jump = -P.aP_dt;
+                    if (n0 + g * 4u + k == S.eP) jump = pois_event(S, P, K, path);
+                }
+            }
+            if (DICH) jump += (dm & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
+            pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, jump, dcur, dnext);
+            dcur = dnext;
+        }
+        pm >>= 4;
+        dm >>= 4;
+        if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
+    }
+}
+
+// Steps n in [n, n_end): edges one at a time, whole 32-step chunks with the
+// events of each chunk drawn up front.  All 32 lanes of the warp must call
+// this together.
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                           uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
@@ -331,21 +426,14 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
         float dcur = drive_at(n, P);
         for (; n + 32u <= n_end; n += 32u) {
             const float dch = drive_at(n + 1u + lane, P);
-#pragma unroll 1
-            for (uint32_t g = 0; g < 8u; ++g) {
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if (P.gauss_on) w = stream(K, P.c1_gauss, path, (n >> 2) + g);
-#pragma unroll
-                for (uint32_t k = 0; k < 4u; ++k) {
-                    const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
-                    const float dxi = P.gauss_on ? gauss_inc<GAUSS>(w, k, P) : 0.0f;
-                    float jump = 0.0f;
-                    if (POIS) jump += pois_step(S, P, K, path);
-                    if (DICH) jump += dich_step(S, P, K, path);
-                    pc_step<MODEL, ACC>(S, P, dxi, jump, dcur, dnext);
-                    dcur = dnext;
-                }
-            }
+            uint32_t pm, dm;
+            float z0, z1, z2;
+            if (chunk_events<POIS, DICH>(S, P, K, path, n, pm, z0, z1, z2, dm))
+                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, true>(S, P, K, path, n, dch, dcur, pm, z0,
+                                                                 z1, z2, dm);
+            else
+                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, false>(S, P, K, path, n, dch, dcur, pm,
+                                                                  z0, z1, z2, dm);
             if (ACC) {
                 S.svd += (double)S.sv;
                 S.sv2d += (double)S.sv2;
@@ -369,19 +457,20 @@ __device__ __forceinline__ void init_path(PathState& S, const PointConsts& P, co
     fold<MODEL>(S);
     S.sv = S.sv2 = 0.0f;
     S.svd = S.sv2d = 0.0;
-    S.sP = 0; S.jP = 0u; S.pw2 = S.pw3 = 0u;
-    S.sD = 0; S.jD = 0u; S.dst = 0u; S.gam = 0.0f; S.dw1 = S.dw2 = S.dw3 = 0u;
+    S.eP = 0xffffffffu; S.JP = 0u; S.pw2 = S.pw3 = 0u;
+    S.eD = 0xffffffffu; S.JD = 0u; S.dst = 0u; S.dw1 = S.dw2 = S.dw3 = 0u;
     if (POIS) {
-        const uint4 e = stream(K, P.c1_pois, path, 0u);        // event 0: countdown only
-        S.sP = wait_steps(e.x, P.pois_cl2, P.inv_lambda, P.dt64);
+        const uint4 e = stream(K, P.c1_pois, path, 0u);        // index 0: initial countdown
+        S.eP = (uint32_t)wait_steps(e.x, P.pois_cl2, P.inv_lambda, P.dt64);
+        S.JP = 1u;
         S.pw2 = e.z; S.pw3 = e.w;
     }
     if (DICH) {
         S.dst = (w.z >> 8) < P.d0_thresh ? 1u : 0u;             // stationary start
-        S.gam = S.dst ? P.Fb_dt : P.mFa_dt;
         const uint4 e = stream(K, P.c1_dich, path, 0u);
-        S.sD = S.dst ? wait_steps(e.x, P.mub_cl2, P.inv_mub, P.dt64)
-                     : wait_steps(e.x, P.mua_cl2, P.inv_mua, P.dt64);
+        S.eD = S.dst ? (uint32_t)wait_steps(e.x, P.mub_cl2, P.inv_mub, P.dt64)
+                     : (uint32_t)wait_steps(e.x, P.mua_cl2, P.inv_mua, P.dt64);
+        S.JD = 1u;
         S.dw1 = e.y; S.dw2 = e.z; S.dw3 = e.w;
     }
 }
@@ -399,6 +488,7 @@ __device__ __forceinline__ void simulate_path(const PointConsts& P, const Launch
     PathState S;
     init_path<MODEL, POIS, DICH>(S, P, K, path);
     run_steps<MODEL, POIS, DICH, GAUSS, false>(S, P, K, path, lane, 0u, P.n_tr);
+    if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
     S.c_i = S.c;
     S.kf_i = S.kf;
     run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane, P.n_tr,
@@ -410,8 +500,8 @@ __device__ __forceinline__ void simulate_path(const PointConsts& P, const Launch
     R.sum_v = S.svd + (double)S.sv;
     R.sum_v2 = S.sv2d + (double)S.sv2;
     R.v_f = S.v;
-    R.jP = S.jP;
-    R.jD = S.jD;
+    R.jP = POIS ? S.JP - 1u : 0u;     // index of the last event that happened
+    R.jD = DICH ? S.JD - 1u : 0u;
 }
 
 // ---------------------------------------------------------------- reductions

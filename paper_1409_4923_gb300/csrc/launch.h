@@ -19,8 +19,10 @@ cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const Point
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                          int block_threads, int grid_blocks, int sm_count, cudaStream_t st);
 
-// Inertial-washboard scan kernel over an item table of (point, first path).
-cudaError_t launch_scan(bool pois, bool dich, const PointConsts* pts_dev, const uint2* items_dev,
+// Inertial-washboard scan kernel over an item table of (point, first path);
+// gauss is 0 (no Gaussian noise) or the three-point law.
+cudaError_t launch_scan(bool pois, bool dich, int gauss, const PointConsts* pts_dev,
+                        const uint2* items_dev,
                         const LaunchConsts& K, const Workspace& ws, int block_threads,
                         int grid_blocks, int sm_count, cudaStream_t st);
 

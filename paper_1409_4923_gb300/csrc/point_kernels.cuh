@@ -69,6 +69,8 @@ cudaError_t launch_point_model(bool pois, bool dich, int gauss, const PointConst
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) \
         return launch_point_t<MODEL, PO, DI, GA>(P, K, ws, po, bt, gb, sm, st);
+    SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
+    SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
     SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
     SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
     SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
@@ -82,6 +84,8 @@ int blocks_per_sm_model(bool pois, bool dich, int gauss, int bt)
 {
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) return blocks_per_sm_t<MODEL, PO, DI, GA>(bt);
+    SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
+    SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
     SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
     SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
     SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
