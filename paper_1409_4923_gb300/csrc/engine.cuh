@@ -133,13 +133,15 @@ __device__ __forceinline__ int32_t wait_steps(uint32_t w, float cl2, double inv_
     return (int32_t)fl;
 }
 
-// Drive a cos(omega t_n) + F at step n, times dt in coordinate units.
+// Drive a cos(omega t_n) + F at step n, times dt in coordinate units.  The
+// phase n omega dt / 2 pi is exact modulo one period in 64-bit fixed point;
+// its top 32 bits give an angle in [-pi, pi) for the SFU cosine.
 __device__ __forceinline__ float drive_at(uint32_t n, const PointConsts& P)
 {
     const uint64_t ph = (uint64_t)n * P.phase_step;       // fraction of a period, mod 1
     const int32_t hi = (int32_t)(uint32_t)(ph >> 32);     // in [-1/2, 1/2) periods, Q0.32
-    const float two_r = (float)hi * 0x1p-31f;
-    return fmaf(P.a_dt, cospif(two_r), P.F_dt);
+    const float ang = (float)hi * 1.4629180792671596e-09f;   // 2 pi / 2^32
+    return fmaf(P.a_dt, cos_sfu(ang), P.F_dt);
 }
 
 // ---------------------------------------------------------------- path state
@@ -371,18 +373,25 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
     }
 }
 
-// One 32-step chunk from n0: 8 groups of 4 steps, one Philox call per group
-// for the Gaussian words, the drive of step n0 + 1 + l in lane l (shuffled to
-// every lane per step), jump events from the chunk masks (FAST) or inline.
+// One 32-step chunk from n0: 8 groups of 4 steps, the drive of step
+// n0 + 1 + l in lane l (shuffled to every lane per step), jump events from
+// the chunk masks (FAST) or inline.  w holds the Gaussian words of the
+// chunk's first group; each group draws the next group's words while it
+// integrates (so the Philox multiplies interleave with the step arithmetic),
+// and w returns holding those of the group after the chunk.
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST>
 __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                             uint32_t path, uint32_t n0, float dch, float& dcur,
-                                            uint32_t pm, float z0, float z1, float z2, uint32_t dm)
+                                            uint4& w, uint32_t pm, float z0, float z1, float z2,
+                                            uint32_t dm)
 {
-#pragma unroll 1
+    // two groups per iteration unless the Poisson queue doubles the body
+    // (measured: the unrolled two-variant Poisson chunk runs 15 % slower)
+    constexpr int kGroupUnroll = POIS ? 1 : 2;
+#pragma unroll kGroupUnroll
     for (uint32_t g = 0; g < 8u; ++g) {
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (GAUSS != 0) w = stream(K, P.c1_gauss, path, (n0 >> 2) + g);
+        uint4 wn = make_uint4(0u, 0u, 0u, 0u);
+        if (GAUSS != 0) wn = stream(K, P.c1_gauss, path, (n0 >> 2) + g + 1u);
 #pragma unroll
         for (uint32_t k = 0; k < 4u; ++k) {
             const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
@@ -403,6 +412,7 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
             pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, jump, dcur, dnext);
             dcur = dnext;
         }
+        w = wn;
         pm >>= 4;
         dm >>= 4;
         if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
@@ -410,8 +420,9 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
 }
 
 // Steps n in [n, n_end): edges one at a time, whole 32-step chunks with the
-// events of each chunk drawn up front.  All 32 lanes of the warp must call
-// this together.
+// events of each chunk drawn up front.  The FP32 window partials are moved to
+// the FP64 accumulators every 8 chunks (256 steps).  All 32 lanes of the warp
+// must call this together.
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                           uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
@@ -424,21 +435,25 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
     }
     if (n + 32u <= n_end) {
         float dcur = drive_at(n, P);
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (GAUSS != 0) w = stream(K, P.c1_gauss, path, n >> 2);
+        uint32_t since_flush = 0u;
         for (; n + 32u <= n_end; n += 32u) {
             const float dch = drive_at(n + 1u + lane, P);
             uint32_t pm, dm;
             float z0, z1, z2;
             if (chunk_events<POIS, DICH>(S, P, K, path, n, pm, z0, z1, z2, dm))
-                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, true>(S, P, K, path, n, dch, dcur, pm, z0,
-                                                                 z1, z2, dm);
+                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, true>(S, P, K, path, n, dch, dcur, w, pm,
+                                                                 z0, z1, z2, dm);
             else
-                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, false>(S, P, K, path, n, dch, dcur, pm,
+                chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, false>(S, P, K, path, n, dch, dcur, w, pm,
                                                                   z0, z1, z2, dm);
-            if (ACC) {
+            if (ACC && ++since_flush == 8u) {
                 S.svd += (double)S.sv;
                 S.sv2d += (double)S.sv2;
                 S.sv = 0.0f;
                 S.sv2 = 0.0f;
+                since_flush = 0u;
             }
         }
     }
