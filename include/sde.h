@@ -178,6 +178,37 @@ int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
  * and the device's SM count (host outputs). */
 int sde_occupancy(sde_ctx* ctx, int block_threads, int* blocks_per_sm, int* sm_count);
 
+/* Largest path count of sde_run_noalloc. */
+#define SDE_NOALLOC_MAX_PATHS 2097152u   /* 2^21 */
+
+/* A Monte Carlo run, as sde_run + the device part of sde_stats, that
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.  For
+ * callers that cannot allocate device memory: code under a memory pool or
+ * arena that must own every allocation, real-time loops that may not call
+ * cudaMalloc / cudaFree (both can synchronise the whole device), hosts that
+ * forbid allocation after start-up.  The paper has no counterpart; it is an
+ * integration aid.
+ *   model, p, seed, paths, dt, n_transient, n_avg: as sde_create + sde_run
+ *     (p is a host struct, copied); paths <= SDE_NOALLOC_MAX_PATHS, else
+ *     SDE_EINVAL;
+ *   cuda_stream: cudaStream_t to enqueue on (NULL = legacy default stream);
+ *     the call returns after enqueueing, without synchronising;
+ *   out5: caller-owned DEVICE array of 5 doubles that receives the same FP64
+ *     sums as sde_stats_t.sums (paths, sum vbar, sum vbar^2, sum v, sum v^2);
+ *   status_out: caller-owned DEVICE int32 (or NULL) that receives SDE_OK.
+ * Scratch (the work counter, the status word and 5 doubles per 32 paths,
+ * 2.6 MB in all) is one file-scope device array of fixed size, held by every
+ * GPU that loads this library until the process exits.  All calls share it
+ * and it keeps the last call's contents (each call clears what must start at
+ * zero), so calls whose work overlaps on the GPU (other streams, other host
+ * threads on the same device) race: serialise them.  The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Errors: SDE_EINVAL, SDE_ECUDA;
+ * the message is sde_last_error(NULL). */
+int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t seed, uint64_t paths,
+                    double dt, uint64_t n_transient, uint64_t n_avg, void* cuda_stream,
+                    double* out5, int32_t* status_out);
+
 /* Free everything the context owns (waits for its stream first). */
 void sde_destroy(sde_ctx* ctx);
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "sde.h"
+#include "capi_internal.h"
 #include "launch.h"
 
 using namespace sde;
@@ -58,7 +59,7 @@ struct sde_ctx {
 
 static std::string g_create_error;
 
-static int fail(sde_ctx* c, int code, const std::string& msg)
+int fail(sde_ctx* c, int code, const std::string& msg)
 {
     if (c) c->err = msg; else g_create_error = msg;
     return code;
@@ -74,7 +75,7 @@ static int cuda_fail(sde_ctx* c, cudaError_t e, const char* what)
 
 static bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
 
-static int validate_params(sde_ctx* c, sde_model model, const sde_params* p)
+int validate_params(sde_ctx* c, sde_model model, const sde_params* p)
 {
     if (!p) return fail(c, SDE_EINVAL, "params is NULL");
     if ((int)model < 0 || (int)model > 2) return fail(c, SDE_EINVAL, "unknown model");
@@ -95,7 +96,7 @@ static int validate_params(sde_ctx* c, sde_model model, const sde_params* p)
     return SDE_OK;
 }
 
-static int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
+int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
 {
     if (paths < 1 || paths > 0xFFFFFFC0ull) return fail(c, SDE_EINVAL, "paths must be in [1, 2^32 - 64]");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDE_EINVAL, "dt must be finite and > 0");
@@ -106,7 +107,7 @@ static int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, ui
 }
 
 // Gaussian kernel variant: none (flag off or zero intensity), three-point, Gaussian.
-static int gauss_kind(const sde_params& p)
+int gauss_kind(const sde_params& p)
 {
     if (!(p.noise_flags & SDE_NOISE_GAUSS) || !(p.Q > 0.0)) return 0;
     return (p.noise_flags & SDE_GAUSS_NORMAL) ? kGaussNormal : kGauss3Point;
@@ -115,7 +116,7 @@ static int gauss_kind(const sde_params& p)
 // Kernel constants of one point, from the FP64 parameters.  Coordinates:
 // washboards integrate c = 2 pi x (so the SFU cosine takes c directly), the
 // piecewise-linear model integrates x; noise is scaled into those units.
-static int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,
+int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,
                       uint64_t n_tr, uint64_t n_avg, uint32_t first_item, PointConsts& P)
 {
     std::memset(&P, 0, sizeof(P));
@@ -183,7 +184,7 @@ static int make_point(sde_ctx* c, sde_model model, const sde_params& p, double d
     return SDE_OK;
 }
 
-static LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns)
+LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns)
 {
     LaunchConsts K;
     std::memset(&K, 0, sizeof(K));

@@ -90,6 +90,9 @@ def lib():
         "sde_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "sde_occupancy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
+        "sde_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
+                                           ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64,
+                                           ctypes.c_uint64, _P, _P, _P]),
         "sde_destroy": (None, [_P]),
         "sde_last_error": (ctypes.c_char_p, [_P]),
         "sde_version": (ctypes.c_char_p, []),
@@ -226,6 +229,24 @@ class Engine:
         _check(self._ctx, lib().sde_philox_words(self._ctx, ctr.ctypes.data, ctr.shape[0],
                                                  int(seed), out.ctypes.data))
         return out
+
+
+NOALLOC_MAX_PATHS = 1 << 21
+
+
+def run_noalloc(model, params: Params, seed, paths, dt, n_transient, n_avg, out5, status=None,
+                stream=None):
+    """sde_run_noalloc: a run that allocates nothing, for callers that cannot allocate
+    device memory.  out5: caller-owned CUDA float64 tensor of 5 elements (the FP64
+    sums); status: optional CUDA int32 tensor of 1 element.  Enqueues and returns."""
+    if not out5.is_cuda or out5.dtype.itemsize != 8 or out5.numel() < 5:
+        raise ValueError("out5 must be a CUDA float64 tensor of >= 5 elements")
+    st = None if status is None else ctypes.c_void_p(status.data_ptr())
+    rc = lib().sde_run_noalloc(int(model), ctypes.byref(params), int(seed), int(paths), float(dt),
+                               int(n_transient), int(n_avg), _stream_handle(stream),
+                               ctypes.c_void_p(out5.data_ptr()), st)
+    if rc != SDE_OK:
+        raise SdeError(rc, lib().sde_last_error(None).decode())
 
 
 def version():
