@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["point_inertial.cu", "point_overdamped_washboard.cu", "point_overdamped_pwl.cu",
-         "aux_kernels.cu", "capi.cu", "noalloc.cu"]
+         "aux_kernels.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
 
 
 def nvcc():
@@ -29,7 +29,7 @@ def nvcc():
 
 def _sources():
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(INCLUDE, "sde.h"))
+    deps += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return deps
 
 

@@ -1,0 +1,684 @@
+// mlp.cu -- surrogate network: BF16 tensor-core GEMMs with fused epilogues,
+// loss, Adam and the C ABI of include/sde_mlp.h.
+//
+// Every GEMM of the forward and backward pass is one templated kernel: a
+// 64 x 64 output tile per 128-thread block, 32-deep K slices staged in shared
+// memory, 2 x 2 warps of 32 x 32, mma.m16n8k16 BF16 x BF16 -> FP32 with
+// fragments loaded by ldmatrix (transposed where the operand is stored the
+// other way round).  Epilogues fuse the bias, SiLU and its derivative.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "sde.h"
+#include "sde_mlp.h"
+
+namespace {
+
+constexpr int kIn = SDE_MLP_IN, kInPad = 16, kH = SDE_MLP_HIDDEN, kOut = SDE_MLP_OUT, kOutPad = 8;
+constexpr uint64_t kMaxBatch = 65536;
+constexpr int kSplitRows = 256;        // batch rows per split of the weight-gradient GEMMs
+
+// Offsets in the flat parameter vector.
+constexpr size_t oW1 = 0, oB1 = oW1 + kH * kInPad, oW2 = oB1 + kH, oB2 = oW2 + kH * kH,
+                 oW3 = oB2 + kH, oB3 = oW3 + kH * kH, oW4 = oB3 + kH, oB4 = oW4 + kOutPad * kH,
+                 kNParams = oB4 + kOutPad;
+static_assert(kNParams == SDE_MLP_NPARAMS, "parameter layout");
+
+enum { EPI_F32 = 0, EPI_FWD_SILU = 1, EPI_FWD_LINEAR = 2, EPI_BWD_DSILU = 3 };
+
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16* A; int lda;
+    const __nv_bfloat16* B; int ldb;
+    float* C; int ldc;                  // EPI_F32 / EPI_FWD_LINEAR output, EPI_FWD_SILU pre-activation (may be null)
+    __nv_bfloat16* O; int ldo;          // BF16 output (SiLU activation or back-propagated gradient)
+    const float* bias;                  // EPI_FWD_*
+    const float* H; int ldh;            // EPI_BWD_DSILU: pre-activation of the layer below
+    int k_split;                        // rows of K per blockIdx.z (split-K), 0 = all
+    size_t c_split_stride;              // elements between the outputs of consecutive splits
+};
+
+__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float dsilu(float x)
+{
+    const float s = 1.0f / (1.0f + __expf(-x));
+    return s * (1.0f + x * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int BM = 64, BN = 64, BK = 32;
+
+// C tile (BM x BN) = op(A) op(B).  A_KM: A stored [K][M] (else [M][K]); B_KN:
+// B stored [K][N] (else [N][K]).  Operands are loaded 8 BF16 at a time; rows
+// or columns outside the matrix are zero-filled.
+template <bool A_KM, bool B_KN, int EPI>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 sA[A_KM ? BK : BM][(A_KM ? BM : BK) + 8];
+    __shared__ __align__(16) __nv_bfloat16 sB[B_KN ? BK : BN][(B_KN ? BN : BK) + 8];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    int kb = 0, ke = g.K;
+    if (g.k_split > 0) {
+        kb = blockIdx.z * g.k_split;
+        ke = min(g.K, kb + g.k_split);
+    }
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        // ---- stage A and B (2 x 16-byte chunks per thread each)
+#pragma unroll
+        for (int c = tid; c < 256; c += 128) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (!A_KM) {
+                const int r = c >> 2, col = (c & 3) * 8;
+                const int gm = m0 + r, gk = k0 + col;
+                if (gm < g.M && gk < ke) v = *(const uint4*)(g.A + (size_t)gm * g.lda + gk);
+                *(uint4*)&sA[r][col] = v;
+            } else {
+                const int r = c >> 3, col = (c & 7) * 8;
+                const int gk = k0 + r, gm = m0 + col;
+                if (gk < ke && gm < g.M) v = *(const uint4*)(g.A + (size_t)gk * g.lda + gm);
+                *(uint4*)&sA[r][col] = v;
+            }
+            uint4 u = make_uint4(0u, 0u, 0u, 0u);
+            if (!B_KN) {
+                const int r = c >> 2, col = (c & 3) * 8;
+                const int gn = n0 + r, gk = k0 + col;
+                if (gn < g.N && gk < ke) u = *(const uint4*)(g.B + (size_t)gn * g.ldb + gk);
+                *(uint4*)&sB[r][col] = u;
+            } else {
+                const int r = c >> 3, col = (c & 7) * 8;
+                const int gk = k0 + r, gn = n0 + col;
+                if (gk < ke && gn < g.N) u = *(const uint4*)(g.B + (size_t)gk * g.ldb + gn);
+                *(uint4*)&sB[r][col] = u;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int mb = wm + mt * 16;
+                if (!A_KM) {
+                    const int r = mb + (lane & 15), col = kk + (lane >> 4) * 8;
+                    ldsm_x4(smem_u32(&sA[r][col]), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+                } else {
+                    const int r = kk + (lane >> 4) * 8 + (lane & 7), col = mb + ((lane >> 3) & 1) * 8;
+                    ldsm_x4_t(smem_u32(&sA[r][col]), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+                }
+            }
+            uint32_t bf[4][2];
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {
+                const int nb = wn + np * 16;
+                uint32_t r0, r1, r2, r3;
+                if (!B_KN) {
+                    const int r = nb + (lane >> 4) * 8 + (lane & 7), col = kk + ((lane >> 3) & 1) * 8;
+                    ldsm_x4(smem_u32(&sB[r][col]), r0, r1, r2, r3);
+                } else {
+                    const int r = kk + ((lane >> 3) & 1) * 8 + (lane & 7), col = nb + (lane >> 4) * 8;
+                    ldsm_x4_t(smem_u32(&sB[r][col]), r0, r1, r2, r3);
+                }
+                bf[np * 2][0] = r0; bf[np * 2][1] = r1;
+                bf[np * 2 + 1][0] = r2; bf[np * 2 + 1][1] = r3;
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
+        }
+        __syncthreads();
+    }
+
+    // ---- epilogue: thread holds rows g, g+8 and columns 2t, 2t+1 of each 16 x 8 tile
+    const int gi = lane >> 2, ti = lane & 3;
+    float* C = g.C;
+    if (EPI == EPI_F32 && g.k_split > 0) C += (size_t)blockIdx.z * g.c_split_stride;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm + mt * 16 + gi + h * 8;
+                if (m >= g.M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int n = n0 + wn + nt * 8 + ti * 2 + e;
+                    if (n >= g.N) continue;
+                    float v = acc[mt][nt][h * 2 + e];
+                    if (EPI == EPI_F32) {
+                        C[(size_t)m * g.ldc + n] = v;
+                    } else if (EPI == EPI_FWD_LINEAR) {
+                        C[(size_t)m * g.ldc + n] = v + g.bias[n];
+                    } else if (EPI == EPI_FWD_SILU) {
+                        v += g.bias[n];
+                        if (C) C[(size_t)m * g.ldc + n] = v;
+                        g.O[(size_t)m * g.ldo + n] = __float2bfloat16_rn(silu(v));
+                    } else {
+                        v *= dsilu(g.H[(size_t)m * g.ldh + n]);
+                        g.O[(size_t)m * g.ldo + n] = __float2bfloat16_rn(v);
+                    }
+                }
+            }
+}
+
+template <bool A_KM, bool B_KN, int EPI>
+cudaError_t gemm(const GemmArgs& a, int splits, cudaStream_t st)
+{
+    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, splits > 0 ? splits : 1);
+    gemm_bf16_kernel<A_KM, B_KN, EPI><<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Raw inputs -> mapped BF16 inputs [Mp][16] (rows >= M and columns >= 7 zero).
+__global__ void input_map_kernel(const float* __restrict__ x, uint64_t M, uint64_t Mp,
+                                 const float* __restrict__ maps, uint32_t log_mask,
+                                 __nv_bfloat16* __restrict__ X)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mp * kInPad) return;
+    const uint64_t m = i / kInPad;
+    const int c = (int)(i % kInPad);
+    float v = 0.0f;
+    if (m < M && c < kIn) {
+        float r = x[m * kIn + c];
+        if (log_mask & (1u << c)) r = log10f(r);
+        v = (r - maps[c]) * maps[kIn + c];
+    }
+    X[i] = __float2bfloat16_rn(v);
+}
+
+// Standardised outputs y' [Mp][8] -> y [M][2] in raw units.
+__global__ void output_map_kernel(const float* __restrict__ yp, uint64_t M,
+                                  const float* __restrict__ maps, float* __restrict__ y)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * kOut) return;
+    const uint64_t m = i / kOut;
+    const int o = (int)(i % kOut);
+    y[i] = yp[m * kOutPad + o] * maps[2 * kIn + kOut + o] + maps[2 * kIn + o];
+}
+
+// Loss of the standardised outputs and its gradient dY' = (y' - t') / M
+// (BF16, padded columns zero).  One block; fixed-order reduction.
+__global__ void __launch_bounds__(1024) loss_kernel(const float* __restrict__ yp, const float* __restrict__ t,
+                                                    uint64_t M, uint64_t Mp, const float* __restrict__ maps,
+                                                    __nv_bfloat16* __restrict__ dY, float* __restrict__ loss_out,
+                                                    double* __restrict__ loss64)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    const float invM = 1.0f / (float)M;
+    for (uint64_t i = threadIdx.x; i < Mp * kOutPad; i += blockDim.x) {
+        const uint64_t m = i / kOutPad;
+        const int o = (int)(i % kOutPad);
+        float d = 0.0f;
+        if (m < M && o < kOut) {
+            const float tp = (t[m * kOut + o] - maps[2 * kIn + o]) / maps[2 * kIn + kOut + o];
+            const float r = yp[m * kOutPad + o] - tp;
+            s += 0.5 * (double)r * (double)r;
+            d = r * invM;
+        }
+        dY[i] = __float2bfloat16_rn(d);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double L = red[0] / (double)M;
+        if (loss_out) *loss_out = (float)L;
+        if (loss64) *loss64 = L;
+    }
+}
+
+// Sum of split-K partials (fixed order) into the gradient vector.
+__global__ void split_reduce_kernel(const float* __restrict__ part, int splits, size_t n, float* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * n + i];
+    out[i] = s;
+}
+
+// Column sums of a BF16 [Mp][N] matrix (bias gradients), one thread per column.
+__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ G, uint64_t Mp, int N, int ld,
+                              float* __restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (uint64_t m = 0; m < Mp; ++m) s += __bfloat162float(G[m * ld + n]);
+    out[n] = s;
+}
+
+// Adam on the flat FP32 parameters; refreshes the BF16 copies.
+__global__ void adam_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
+                            float* __restrict__ m1, float* __restrict__ m2, size_t n, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    const float wi = w[i] - lr * (a * c1) / (sqrtf(b * c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+unsigned nblk(size_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct sde_mlp {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    float* w = nullptr;              // FP32 master parameters
+    __nv_bfloat16* wb = nullptr;     // BF16 copies
+    float* grad = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    float* maps = nullptr;           // shift[7], scale[7], out_shift[2], out_scale[2]
+    uint32_t log_mask = 0;
+    uint64_t step = 0;
+    // activation workspace for up to cap rows
+    uint64_t cap = 0;
+    __nv_bfloat16* X = nullptr;      // [cap][16]
+    float* H[3] = {nullptr, nullptr, nullptr};                 // [cap][256] pre-activations
+    __nv_bfloat16* A[3] = {nullptr, nullptr, nullptr};         // [cap][256] activations
+    float* Yp = nullptr;             // [cap][8]
+    __nv_bfloat16* dY = nullptr;     // [cap][8]
+    __nv_bfloat16* dH[3] = {nullptr, nullptr, nullptr};        // [cap][256]
+    float* part = nullptr;           // split-K partials
+    size_t part_elems = 0;
+    double* loss64 = nullptr;
+    double* host_loss = nullptr;
+};
+
+static std::string g_mlp_error;
+
+static int mfail(sde_mlp* n, int code, const std::string& msg)
+{
+    if (n) n->err = msg; else g_mlp_error = msg;
+    return code;
+}
+
+#define MLP_CUDA(n, call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) \
+    return mfail((n), e_ == cudaErrorMemoryAllocation ? SDE_ENOMEM : SDE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } while (0)
+
+static void free_acts(sde_mlp* n)
+{
+    cudaFree(n->X); n->X = nullptr;
+    for (int i = 0; i < 3; ++i) {
+        cudaFree(n->H[i]); cudaFree(n->A[i]); cudaFree(n->dH[i]);
+        n->H[i] = nullptr; n->A[i] = nullptr; n->dH[i] = nullptr;
+    }
+    cudaFree(n->Yp); cudaFree(n->dY); cudaFree(n->part);
+    n->Yp = nullptr; n->dY = nullptr; n->part = nullptr;
+    n->cap = 0;
+    n->part_elems = 0;
+}
+
+static uint64_t pad64(uint64_t m) { return (m + 63u) & ~(uint64_t)63u; }
+
+static int ensure_acts(sde_mlp* n, uint64_t Mp, bool train)
+{
+    if (Mp <= n->cap && (!train || n->dY)) return SDE_OK;
+    cudaStreamSynchronize(n->stream);
+    free_acts(n);
+    const uint64_t c = Mp;
+    MLP_CUDA(n, cudaMalloc(&n->X, c * kInPad * sizeof(__nv_bfloat16)));
+    for (int i = 0; i < 3; ++i) {
+        MLP_CUDA(n, cudaMalloc(&n->A[i], c * kH * sizeof(__nv_bfloat16)));
+        if (train) {
+            MLP_CUDA(n, cudaMalloc(&n->H[i], c * kH * sizeof(float)));
+            MLP_CUDA(n, cudaMalloc(&n->dH[i], c * kH * sizeof(__nv_bfloat16)));
+        }
+    }
+    MLP_CUDA(n, cudaMalloc(&n->Yp, c * kOutPad * sizeof(float)));
+    if (train) {
+        MLP_CUDA(n, cudaMalloc(&n->dY, c * kOutPad * sizeof(__nv_bfloat16)));
+        const size_t splits = (c + kSplitRows - 1) / kSplitRows;
+        n->part_elems = splits * (size_t)kH * kH;
+        MLP_CUDA(n, cudaMalloc(&n->part, n->part_elems * sizeof(float)));
+    }
+    n->cap = c;
+    return SDE_OK;
+}
+
+// Forward pass on Mp (padded) rows already mapped into n->X; standardised
+// outputs into n->Yp.  store_pre: keep the pre-activations for the backward.
+static cudaError_t forward_rows(sde_mlp* n, uint64_t Mp, bool store_pre)
+{
+    const int M = (int)Mp;
+    GemmArgs a{};
+    a.M = M; a.N = kH; a.K = kInPad; a.A = n->X; a.lda = kInPad; a.B = n->wb + oW1; a.ldb = kInPad;
+    a.C = store_pre ? n->H[0] : nullptr; a.ldc = kH; a.O = n->A[0]; a.ldo = kH; a.bias = n->w + oB1;
+    cudaError_t e = gemm<false, false, EPI_FWD_SILU>(a, 0, n->stream);
+    for (int l = 1; l < 3 && e == cudaSuccess; ++l) {
+        GemmArgs b{};
+        b.M = M; b.N = kH; b.K = kH; b.A = n->A[l - 1]; b.lda = kH;
+        b.B = n->wb + (l == 1 ? oW2 : oW3); b.ldb = kH;
+        b.C = store_pre ? n->H[l] : nullptr; b.ldc = kH; b.O = n->A[l]; b.ldo = kH;
+        b.bias = n->w + (l == 1 ? oB2 : oB3);
+        e = gemm<false, false, EPI_FWD_SILU>(b, 0, n->stream);
+    }
+    if (e == cudaSuccess) {
+        GemmArgs c{};
+        c.M = M; c.N = kOutPad; c.K = kH; c.A = n->A[2]; c.lda = kH; c.B = n->wb + oW4; c.ldb = kH;
+        c.C = n->Yp; c.ldc = kOutPad; c.bias = n->w + oB4;
+        e = gemm<false, false, EPI_FWD_LINEAR>(c, 0, n->stream);
+    }
+    return e;
+}
+
+// Weight gradient dW[N][K] = dH^T X over Mp batch rows (split-K, fixed-order sum).
+static cudaError_t weight_grad(sde_mlp* n, const __nv_bfloat16* dH, int ldh, int N,
+                               const __nv_bfloat16* X, int ldx, int K, uint64_t Mp, float* out)
+{
+    const int splits = (int)((Mp + kSplitRows - 1) / kSplitRows);
+    GemmArgs a{};
+    a.M = N; a.N = K; a.K = (int)Mp; a.A = dH; a.lda = ldh; a.B = X; a.ldb = ldx;
+    a.C = n->part; a.ldc = K; a.k_split = kSplitRows; a.c_split_stride = (size_t)N * K;
+    cudaError_t e = gemm<true, true, EPI_F32>(a, splits, n->stream);
+    if (e != cudaSuccess) return e;
+    split_reduce_kernel<<<nblk((size_t)N * K), 256, 0, n->stream>>>(n->part, splits, (size_t)N * K, out);
+    return cudaGetLastError();
+}
+
+// Loss and gradients (into n->grad) for a batch already in n->X (Mp rows).
+static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_t Mp, float* loss_dev)
+{
+    loss_kernel<<<1, 1024, 0, n->stream>>>(n->Yp, t, M, Mp, n->maps, n->dY, loss_dev, n->loss64);
+    cudaError_t e = cudaGetLastError();
+    // layer 4
+    if (e == cudaSuccess) e = weight_grad(n, n->dY, kOutPad, kOutPad, n->A[2], kH, kH, Mp, n->grad + oW4);
+    if (e == cudaSuccess) {
+        colsum_kernel<<<1, 256, 0, n->stream>>>(n->dY, Mp, kOutPad, kOutPad, n->grad + oB4);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        GemmArgs a{};
+        a.M = (int)Mp; a.N = kH; a.K = kOutPad; a.A = n->dY; a.lda = kOutPad; a.B = n->wb + oW4; a.ldb = kH;
+        a.O = n->dH[2]; a.ldo = kH; a.H = n->H[2]; a.ldh = kH;
+        e = gemm<false, true, EPI_BWD_DSILU>(a, 0, n->stream);
+    }
+    // layers 3, 2 (weights W3, W2) and the input layer
+    const size_t oW[3] = {oW1, oW2, oW3}, oB[3] = {oB1, oB2, oB3};
+    for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
+        const __nv_bfloat16* below = l == 0 ? n->X : n->A[l - 1];
+        const int kin = l == 0 ? kInPad : kH;
+        e = weight_grad(n, n->dH[l], kH, kH, below, kin, kin, Mp, n->grad + oW[l]);
+        if (e == cudaSuccess) {
+            colsum_kernel<<<1, 256, 0, n->stream>>>(n->dH[l], Mp, kH, kH, n->grad + oB[l]);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && l > 0) {
+            GemmArgs a{};
+            a.M = (int)Mp; a.N = kH; a.K = kH; a.A = n->dH[l]; a.lda = kH; a.B = n->wb + oW[l]; a.ldb = kH;
+            a.O = n->dH[l - 1]; a.ldo = kH; a.H = n->H[l - 1]; a.ldh = kH;
+            e = gemm<false, true, EPI_BWD_DSILU>(a, 0, n->stream);
+        }
+    }
+    return e;
+}
+
+extern "C" {
+
+const char* sde_mlp_last_error(const sde_mlp* n) { return n ? n->err.c_str() : g_mlp_error.c_str(); }
+
+int sde_mlp_create(sde_mlp** out, uint64_t seed, void* cuda_stream)
+{
+    if (!out) return mfail(nullptr, SDE_EINVAL, "out is NULL");
+    *out = nullptr;
+    sde_mlp* n = new (std::nothrow) sde_mlp();
+    if (!n) return mfail(nullptr, SDE_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream == nullptr) {
+        e = cudaStreamCreate(&n->stream);
+        n->own_stream = e == cudaSuccess;
+    } else {
+        n->stream = (cudaStream_t)cuda_stream;
+    }
+    const size_t P = kNParams;
+    if (e == cudaSuccess) e = cudaMalloc(&n->w, P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->wb, P * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&n->grad, P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->m1, P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->m2, P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->maps, 32 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&n->loss64, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&n->host_loss, sizeof(double));
+    if (e != cudaSuccess) {
+        mfail(nullptr, SDE_ECUDA, std::string("sde_mlp_create: ") + cudaGetErrorString(e));
+        sde_mlp_destroy(n);
+        return SDE_ECUDA;
+    }
+    // Glorot-uniform weights from a splitmix64 stream, zero biases and padding
+    std::vector<float> h(P, 0.0f);
+    uint64_t s = seed ^ 0x5DEECE66DULL;
+    auto next_u = [&s]() {
+        s += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto fill = [&](size_t off, int rows, int cols, int live_rows, int live_cols) {
+        const double lim = std::sqrt(6.0 / (double)(live_rows + live_cols));
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c)
+                h[off + (size_t)r * cols + c] =
+                    (r < live_rows && c < live_cols) ? (float)((2.0 * next_u() - 1.0) * lim) : 0.0f;
+    };
+    fill(oW1, kH, kInPad, kH, kIn);
+    fill(oW2, kH, kH, kH, kH);
+    fill(oW3, kH, kH, kH, kH);
+    fill(oW4, kOutPad, kH, kOut, kH);
+    float maps[32] = {0};
+    for (int i = 0; i < kIn; ++i) maps[kIn + i] = 1.0f;
+    maps[2 * kIn + kOut] = maps[2 * kIn + kOut + 1] = 1.0f;
+    e = cudaMemcpyAsync(n->maps, maps, sizeof(maps), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    *out = n;
+    if (e != cudaSuccess) return mfail(n, SDE_ECUDA, cudaGetErrorString(e));
+    return sde_mlp_set_params(n, h.data());
+}
+
+int sde_mlp_set_maps(sde_mlp* n, const float* shift, const float* scale, uint32_t log_mask,
+                     const float* out_shift, const float* out_scale)
+{
+    if (!n || !shift || !scale || !out_shift || !out_scale) return SDE_EINVAL;
+    float maps[32] = {0};
+    for (int i = 0; i < kIn; ++i) {
+        if (!std::isfinite(shift[i]) || !std::isfinite(scale[i])) return mfail(n, SDE_EINVAL, "non-finite input map");
+        maps[i] = shift[i];
+        maps[kIn + i] = scale[i];
+    }
+    for (int o = 0; o < kOut; ++o) {
+        if (!std::isfinite(out_shift[o]) || !(out_scale[o] != 0.0f) || !std::isfinite(out_scale[o]))
+            return mfail(n, SDE_EINVAL, "bad output map");
+        maps[2 * kIn + o] = out_shift[o];
+        maps[2 * kIn + kOut + o] = out_scale[o];
+    }
+    if (log_mask >> kIn) return mfail(n, SDE_EINVAL, "log mask has bits beyond the 7 inputs");
+    n->log_mask = log_mask;
+    MLP_CUDA(n, cudaMemcpyAsync(n->maps, maps, sizeof(maps), cudaMemcpyHostToDevice, n->stream));
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    return SDE_OK;
+}
+
+int sde_mlp_set_params(sde_mlp* n, const float* host)
+{
+    if (!n || !host) return SDE_EINVAL;
+    const size_t P = kNParams;
+    MLP_CUDA(n, cudaMemcpyAsync(n->w, host, P * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+    to_bf16_kernel<<<nblk(P), 256, 0, n->stream>>>(n->w, n->wb, P);
+    MLP_CUDA(n, cudaGetLastError());
+    MLP_CUDA(n, cudaMemsetAsync(n->m1, 0, P * sizeof(float), n->stream));
+    MLP_CUDA(n, cudaMemsetAsync(n->m2, 0, P * sizeof(float), n->stream));
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    n->step = 0;
+    return SDE_OK;
+}
+
+int sde_mlp_get_params(sde_mlp* n, float* host)
+{
+    if (!n || !host) return SDE_EINVAL;
+    MLP_CUDA(n, cudaMemcpyAsync(host, n->w, kNParams * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    return SDE_OK;
+}
+
+int sde_mlp_forward(sde_mlp* n, const float* x, uint64_t M, float* y)
+{
+    if (!n || !x || !y || M == 0) return n ? mfail(n, SDE_EINVAL, "bad forward arguments") : SDE_EINVAL;
+    const uint64_t chunk = kMaxBatch;
+    int rc = ensure_acts(n, pad64(M < chunk ? M : chunk), false);
+    if (rc) return rc;
+    for (uint64_t r0 = 0; r0 < M; r0 += chunk) {
+        const uint64_t m = (M - r0) < chunk ? (M - r0) : chunk;
+        const uint64_t Mp = pad64(m);
+        input_map_kernel<<<nblk(Mp * kInPad), 256, 0, n->stream>>>(x + r0 * kIn, m, Mp, n->maps, n->log_mask, n->X);
+        MLP_CUDA(n, cudaGetLastError());
+        MLP_CUDA(n, forward_rows(n, Mp, false));
+        output_map_kernel<<<nblk(m * kOut), 256, 0, n->stream>>>(n->Yp, m, n->maps, y + r0 * kOut);
+        MLP_CUDA(n, cudaGetLastError());
+    }
+    return SDE_OK;
+}
+
+int sde_mlp_gradients(sde_mlp* n, const float* x, const float* t, uint64_t M, float* host_grad,
+                      double* host_loss)
+{
+    if (!n || !x || !t || !host_grad || M == 0 || M > kMaxBatch)
+        return n ? mfail(n, SDE_EINVAL, "bad gradient arguments (1 <= M <= 65536)") : SDE_EINVAL;
+    const uint64_t Mp = pad64(M);
+    int rc = ensure_acts(n, Mp, true);
+    if (rc) return rc;
+    MLP_CUDA(n, cudaMemsetAsync(n->grad, 0, kNParams * sizeof(float), n->stream));
+    input_map_kernel<<<nblk(Mp * kInPad), 256, 0, n->stream>>>(x, M, Mp, n->maps, n->log_mask, n->X);
+    MLP_CUDA(n, cudaGetLastError());
+    MLP_CUDA(n, forward_rows(n, Mp, true));
+    MLP_CUDA(n, backward_rows(n, t, M, Mp, nullptr));
+    MLP_CUDA(n, cudaMemcpyAsync(host_grad, n->grad, kNParams * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    MLP_CUDA(n, cudaMemcpyAsync(n->host_loss, n->loss64, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    if (host_loss) *host_loss = *n->host_loss;
+    return SDE_OK;
+}
+
+int sde_mlp_train_step(sde_mlp* n, const float* x, const float* t, uint64_t M, float lr, float beta1,
+                       float beta2, float eps, float* loss_dev)
+{
+    if (!n || !x || !t || M == 0 || M > kMaxBatch)
+        return n ? mfail(n, SDE_EINVAL, "bad train arguments (1 <= M <= 65536)") : SDE_EINVAL;
+    if (!(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return mfail(n, SDE_EINVAL, "bad Adam hyper-parameters");
+    const uint64_t Mp = pad64(M);
+    int rc = ensure_acts(n, Mp, true);
+    if (rc) return rc;
+    input_map_kernel<<<nblk(Mp * kInPad), 256, 0, n->stream>>>(x, M, Mp, n->maps, n->log_mask, n->X);
+    MLP_CUDA(n, cudaGetLastError());
+    MLP_CUDA(n, forward_rows(n, Mp, true));
+    MLP_CUDA(n, backward_rows(n, t, M, Mp, loss_dev));
+    n->step += 1;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)n->step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)n->step)));
+    adam_kernel<<<nblk(kNParams), 256, 0, n->stream>>>(n->w, n->wb, n->grad, n->m1, n->m2, kNParams, lr, beta1,
+                                                        beta2, eps, c1, c2);
+    MLP_CUDA(n, cudaGetLastError());
+    return SDE_OK;
+}
+
+int sde_mlp_gemm_bf16(sde_mlp* n, int a_layout, int b_layout, uint32_t M, uint32_t N, uint32_t K,
+                      const void* A, uint32_t lda, const void* B, uint32_t ldb, float* C, uint32_t ldc)
+{
+    if (!n || !A || !B || !C || M == 0 || N == 0 || K == 0) return SDE_EINVAL;
+    if ((lda | ldb) & 7u || ((uintptr_t)A | (uintptr_t)B) & 15u)
+        return mfail(n, SDE_EINVAL, "operands need 16-byte aligned rows (leading dimensions % 8 == 0)");
+    if ((a_layout == 0 && K % 8) || (a_layout == 1 && M % 8) || (b_layout == 0 && K % 8) || (b_layout == 1 && N % 8))
+        return mfail(n, SDE_EINVAL, "the contiguous dimension of each operand must be a multiple of 8");
+    GemmArgs g{};
+    g.M = (int)M; g.N = (int)N; g.K = (int)K;
+    g.A = (const __nv_bfloat16*)A; g.lda = (int)lda; g.B = (const __nv_bfloat16*)B; g.ldb = (int)ldb;
+    g.C = C; g.ldc = (int)ldc;
+    cudaError_t e;
+    if (a_layout == 0 && b_layout == 0) e = gemm<false, false, EPI_F32>(g, 0, n->stream);
+    else if (a_layout == 0 && b_layout == 1) e = gemm<false, true, EPI_F32>(g, 0, n->stream);
+    else if (a_layout == 1 && b_layout == 1) e = gemm<true, true, EPI_F32>(g, 0, n->stream);
+    else if (a_layout == 1 && b_layout == 0) e = gemm<true, false, EPI_F32>(g, 0, n->stream);
+    else return mfail(n, SDE_EINVAL, "layout must be 0 or 1");
+    MLP_CUDA(n, e);
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    return SDE_OK;
+}
+
+void sde_mlp_destroy(sde_mlp* n)
+{
+    if (!n) return;
+    if (n->stream || n->own_stream) cudaStreamSynchronize(n->stream);
+    free_acts(n);
+    cudaFree(n->w); cudaFree(n->wb); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2);
+    cudaFree(n->maps); cudaFree(n->loss64);
+    if (n->host_loss) cudaFreeHost(n->host_loss);
+    if (n->own_stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+}  // extern "C"

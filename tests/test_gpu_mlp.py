@@ -1,0 +1,169 @@
+"""GPU tests of the surrogate network's kernels against the FP64 oracle.
+
+Bars: GEMM entries within 1e-5 of the float64 product of the same BF16
+operands, relative to sum |a||b| (FP32 accumulation); forward outputs within
+3 % of the RMS of the standardised output and gradients within 5 % (norm-wise,
+per tensor) of
+the FP64 oracle evaluated on the same BF16-rounded weights (the kernels round
+every activation to BF16, 2^-9 relative, through four layers).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import surrogate
+    return surrogate
+
+
+def bf16_round(a):
+    """Round-to-nearest-even of float32 values to bfloat16, returned as float64."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("a_layout,b_layout", [(0, 0), (0, 1), (1, 1), (1, 0)])
+@pytest.mark.parametrize("M,N,K", [(64, 64, 32), (200, 72, 48), (8, 256, 512), (136, 16, 256)])
+def test_gemm_layouts(S, a_layout, b_layout, M, N, K):
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = bf16_round(rng.standard_normal((M, K)))
+    B = bf16_round(rng.standard_normal((K, N)))
+    want = A @ B
+    bound = np.abs(A) @ np.abs(B)
+    At = A if a_layout == 0 else A.T
+    Bt = B.T if b_layout == 0 else B
+    net = S.Surrogate(0)
+    try:
+        tA = torch.from_numpy(np.ascontiguousarray(At, dtype=np.float32)).to(torch.bfloat16).cuda()
+        tB = torch.from_numpy(np.ascontiguousarray(Bt, dtype=np.float32)).to(torch.bfloat16).cuda()
+        C = net.gemm_bf16(a_layout, b_layout, M, N, K, tA, tB).cpu().numpy().astype(np.float64)
+    finally:
+        net.close()
+    assert np.all(np.abs(C - want) <= 1e-5 * bound + 1e-6)
+
+
+def _random_net(S, seed):
+    rng = np.random.default_rng(seed)
+    net = S.Surrogate(seed)
+    p = net.get_params().astype(np.float64)
+    P = omlp.unflatten(p)
+    P["b1"] = rng.standard_normal(256) * 0.1
+    P["b2"] = rng.standard_normal(256) * 0.1
+    P["b3"] = rng.standard_normal(256) * 0.1
+    P["b4"][:2] = [0.3, -0.2]
+    p = omlp.flatten(P)
+    net.set_params(p.astype(np.float32))
+    shift = np.array([1.0, 4.0, 5.0, 0.0, -2.5, 2.5, 0.25])
+    scale = np.array([2.0, 0.5, 0.5, 3.3, 0.66, 0.4, 4.0])
+    net.set_maps(shift, scale, 1 << 4, np.array([0.1, -3.0]), np.array([0.2, 1.5]))
+    return net, p, (shift, scale, 1 << 4, np.array([0.1, -3.0]), np.array([0.2, 1.5]))
+
+
+def _raw_inputs(rng, M):
+    lo = np.array([0.5, 2.0, 3.0, -0.3, 1e-4, 0.1, 0.01])
+    hi = np.array([1.5, 6.0, 7.0, 0.3, 1e-1, 5.0, 0.5])
+    x = lo + (hi - lo) * rng.random((M, 7))
+    x[:, 4] = 10.0 ** rng.uniform(-4, -1, M)
+    return x
+
+
+def test_forward_matches_oracle(S):
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 1)
+    rng = np.random.default_rng(2)
+    x = _raw_inputs(rng, 3000)                                # ragged: 47 x 64 rows - 8
+    try:
+        y = net.forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
+    finally:
+        net.close()
+    pb = bf16_round(p)
+    xp = omlp.input_map(x.astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    yp, _ = omlp.forward(pb, xp)
+    want = yp * osc + osh
+    # error in standardised output units relative to the output's RMS
+    err = np.abs(y - want) / osc / np.sqrt(np.mean(yp ** 2, axis=0))
+    assert err.max() < 0.03, err.max()
+
+
+def test_gradients_match_oracle(S):
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 3)
+    rng = np.random.default_rng(4)
+    M = 1000
+    x = _raw_inputs(rng, M)
+    t = np.stack([rng.normal(0.1, 0.2, M), rng.normal(-3.0, 1.5, M)], axis=1)
+    try:
+        g, L = net.gradients(torch.from_numpy(x.astype(np.float32)).cuda(),
+                             torch.from_numpy(t.astype(np.float32)).cuda())
+    finally:
+        net.close()
+    pb = bf16_round(p)
+    xp = omlp.input_map(x.astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    tp = (t.astype(np.float32) - osh) / osc
+    L0, g0 = omlp.loss_and_grad(pb, xp, tp)
+    assert abs(L - L0) <= 0.03 * L0
+    G, G0 = omlp.unflatten(g.astype(np.float64)), omlp.unflatten(g0)
+    for name, _ in omlp.SHAPES:
+        rel = np.linalg.norm(G[name] - G0[name]) / (np.linalg.norm(G0[name]) + 1e-30)
+        assert rel < 0.05, (name, rel)
+    assert np.all(G["W1"][:, 7:] == 0) and np.all(G["W4"][2:] == 0)
+
+
+def test_adam_first_step(S):
+    """t = 1: every live parameter moves by -lr sign(g) where the oracle's
+    gradient is clearly non-zero (Adam's closed-form first step)."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 5)
+    rng = np.random.default_rng(6)
+    M, lr = 512, 1e-3
+    x = _raw_inputs(rng, M)
+    t = np.stack([rng.normal(0.1, 0.2, M), rng.normal(-3.0, 1.5, M)], axis=1)
+    try:
+        net.train_step(torch.from_numpy(x.astype(np.float32)).cuda(),
+                       torch.from_numpy(t.astype(np.float32)).cuda(), lr)
+        q = net.get_params().astype(np.float64)
+    finally:
+        net.close()
+    pb = bf16_round(p)
+    xp = omlp.input_map(x.astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    _, g0 = omlp.loss_and_grad(pb, xp, (t.astype(np.float32) - osh) / osc)
+    big = np.abs(g0) > 1e-3 * np.abs(g0).max()
+    step = q - p.astype(np.float32).astype(np.float64)
+    agree = np.abs(step[big] + lr * np.sign(g0[big])) <= 1e-6
+    assert agree.mean() > 0.97, agree.mean()
+    assert np.all(step[~big & (g0 == 0)] == 0)
+
+
+def test_training_fits_a_smooth_function(S):
+    rng = np.random.default_rng(7)
+    N = 1 << 14
+    x = _raw_inputs(rng, N)
+    u = (x - x.min(0)) / (x.max(0) - x.min(0))
+    t = np.stack([np.sin(3 * u[:, 3]) * np.cos(2 * u[:, 1]) + 0.5 * u[:, 0] * u[:, 6],
+                  np.log10(x[:, 4]) + u[:, 2] ** 2], axis=1)
+    net = S.Surrogate(8)
+    try:
+        lo = np.array([0.5, 2.0, 3.0, -0.3, -4.0, 0.1, 0.01])
+        hi = np.array([1.5, 6.0, 7.0, 0.3, -1.0, 5.0, 0.5])
+        net.set_maps((lo + hi) / 2, 2.0 / (hi - lo), 1 << 4, t.mean(0), t.std(0))
+        X = torch.from_numpy(x.astype(np.float32)).cuda()
+        T = torch.from_numpy(t.astype(np.float32)).cuda()
+        hist = net.fit(X, T, epochs=60, batch=1024, lr=2e-3)
+        y = net.forward(X).cpu().numpy()
+    finally:
+        net.close()
+    assert hist[-1] < 0.05 * hist[0]
+    rmse = np.sqrt(np.mean((y - t) ** 2, axis=0)) / t.std(0)
+    assert np.all(rmse < 0.15), rmse
