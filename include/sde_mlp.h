@@ -66,8 +66,7 @@ int sde_mlp_gradients(sde_mlp* net, const float* x, const float* t, uint64_t M,
 
 /* One Adam step (beta1, beta2, eps, learning rate lr) on the batch (x, t) of
  * M <= 65536 rows (device arrays).  loss_dev (device float or NULL) receives
- * the batch loss before the step.  Asynchronous; graph-capturable after the
- * first call with the same M. */
+ * the batch loss before the step.  Asynchronous. */
 int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M, float lr,
                        float beta1, float beta2, float eps, float* loss_dev);
 
@@ -79,6 +78,20 @@ int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M,
 int sde_mlp_gemm_bf16(sde_mlp* net, int a_layout, int b_layout, uint32_t M, uint32_t N,
                       uint32_t K, const void* A, uint32_t lda, const void* B, uint32_t ldb,
                       float* C, uint32_t ldc);
+
+/* Selection step of the surrogate-guided scan over an nx x ny grid (row-major,
+ * index i * ny + j; all arrays device).  v1, v2: <v> predicted by two
+ * independently trained networks; lse: their mean log10 stderr of the Monte
+ * Carlo label; se_scale: factor from the label's path count to the re-run's
+ * (sqrt(N_label / N_rerun)).  Point p is flagged (flags[p] = 1) when
+ *   - its predicted model error kappa |v1 - v2| + r0 exceeds tol, or
+ *   - its predicted Monte Carlo stderr se_scale 10^lse exceeds se_tol, or
+ *   - the sign of (v1 + v2) / 2 differs from that of a grid 4-neighbour.
+ * `count` (device u32, accumulated) receives the number of flagged points.
+ * Asynchronous on the network's stream. */
+int sde_guided_flags(sde_mlp* net, const float* v1, const float* v2, const float* lse,
+                     uint32_t nx, uint32_t ny, float kappa, float r0, float se_scale, float tol,
+                     float se_tol, uint8_t* flags, uint32_t* count);
 
 void sde_mlp_destroy(sde_mlp* net);
 const char* sde_mlp_last_error(const sde_mlp* net);

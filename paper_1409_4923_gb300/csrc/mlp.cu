@@ -321,6 +321,32 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
 
 unsigned nblk(size_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Flags of the surrogate-guided scan: predicted model error above tol,
+// predicted Monte Carlo stderr above se_tol, or a sign change of the
+// predicted <v> against a 4-neighbour.
+__global__ void guided_flags_kernel(const float* __restrict__ v1, const float* __restrict__ v2,
+                                    const float* __restrict__ lse, uint32_t nx, uint32_t ny, float kappa,
+                                    float r0, float se_scale, float tol, float se_tol,
+                                    uint8_t* __restrict__ flags, uint32_t* __restrict__ count)
+{
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (uint64_t)nx * ny) return;
+    const uint32_t i = (uint32_t)(p / ny), j = (uint32_t)(p % ny);
+    const float v = 0.5f * (v1[p] + v2[p]);
+    const float model_err = kappa * fabsf(v1[p] - v2[p]) + r0;
+    const float se = se_scale * exp10f(lse[p]);
+    bool f = !(model_err <= tol) || !(se <= se_tol);
+    const bool neg = v < 0.0f;
+    auto differs = [&](uint64_t q) { return ((0.5f * (v1[q] + v2[q])) < 0.0f) != neg; };
+    if (i > 0 && differs(p - ny)) f = true;
+    if (i + 1 < nx && differs(p + ny)) f = true;
+    if (j > 0 && differs(p - 1)) f = true;
+    if (j + 1 < ny && differs(p + 1)) f = true;
+    flags[p] = f ? 1 : 0;
+    const unsigned ballot = __ballot_sync(__activemask(), f);
+    if (f && (threadIdx.x & 31u) == (uint32_t)(__ffs(ballot) - 1)) atomicAdd(count, (uint32_t)__popc(ballot));
+}
+
 }  // namespace
 
 struct sde_mlp {
@@ -666,6 +692,18 @@ int sde_mlp_gemm_bf16(sde_mlp* n, int a_layout, int b_layout, uint32_t M, uint32
     else return mfail(n, SDE_EINVAL, "layout must be 0 or 1");
     MLP_CUDA(n, e);
     MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    return SDE_OK;
+}
+
+int sde_guided_flags(sde_mlp* n, const float* v1, const float* v2, const float* lse, uint32_t nx,
+                     uint32_t ny, float kappa, float r0, float se_scale, float tol, float se_tol, uint8_t* flags,
+                     uint32_t* count)
+{
+    if (!n || !v1 || !v2 || !lse || !flags || !count || nx == 0 || ny == 0) return SDE_EINVAL;
+    const uint64_t total = (uint64_t)nx * ny;
+    guided_flags_kernel<<<nblk(total), 256, 0, n->stream>>>(v1, v2, lse, nx, ny, kappa, r0, se_scale, tol,
+                                                            se_tol, flags, count);
+    MLP_CUDA(n, cudaGetLastError());
     return SDE_OK;
 }
 

@@ -34,6 +34,8 @@ def _lib():
             "sde_mlp_gemm_bf16": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
                                                  ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_uint32,
                                                  P, ctypes.c_uint32, P, ctypes.c_uint32]),
+            "sde_guided_flags": (ctypes.c_int, [P, P, P, P, ctypes.c_uint32, ctypes.c_uint32, f, f, f,
+                                                f, f, P, P]),
             "sde_mlp_destroy": (None, [P]),
             "sde_mlp_last_error": (ctypes.c_char_p, [P]),
         }
@@ -110,27 +112,28 @@ class Surrogate:
             self._net, _ptr(x), _ptr(t), x.shape[0], float(lr), float(beta1), float(beta2),
             float(eps), _ptr(loss_out) if loss_out is not None else None))
 
-    def fit(self, X, T, epochs=200, batch=4096, lr=1e-3, lr_final=1e-5, seed=0):
-        """Adam with a cosine learning-rate decay over shuffled minibatches.
-        X, T: CUDA float32 [N, 7] and [N, 2].  Returns the mean batch loss per epoch."""
+    def fit(self, X, T, steps=8000, batch=512, lr=2e-3, lr_final=2e-5, seed=0):
+        """Adam with a cosine learning-rate decay over `steps` minibatches drawn
+        (device-side) from shuffled epochs.  X, T: CUDA float32 [N, 7] and [N, 2].
+        Returns the batch losses (numpy, one per step)."""
         import torch
         n = X.shape[0]
+        batch = min(batch, n)
         g = torch.Generator(device=X.device)
         g.manual_seed(seed)
-        steps_per_epoch = max(1, n // batch)
-        total = epochs * steps_per_epoch
-        losses = torch.zeros(total, dtype=torch.float32, device=X.device)
-        k = 0
-        for ep in range(epochs):
-            perm = torch.randperm(n, device=X.device, generator=g)
-            for s in range(steps_per_epoch):
-                idx = perm[s * batch:(s + 1) * batch]
-                xb = X.index_select(0, idx).contiguous()
-                tb = T.index_select(0, idx).contiguous()
-                lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, total - 1)))
-                self.train_step(xb, tb, lr_k, loss_out=losses[k:k + 1])
-                k += 1
-        return losses.view(epochs, steps_per_epoch).mean(1).cpu().numpy()
+        per_epoch = max(1, n // batch)
+        losses = torch.zeros(steps, dtype=torch.float32, device=X.device)
+        perm = None
+        for k in range(steps):
+            s = k % per_epoch
+            if s == 0:
+                perm = torch.randperm(n, device=X.device, generator=g)
+            idx = perm[s * batch:(s + 1) * batch]
+            xb = X.index_select(0, idx)
+            tb = T.index_select(0, idx)
+            lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+            self.train_step(xb, tb, lr_k, loss_out=losses[k:k + 1])
+        return losses.cpu().numpy()
 
     def gemm_bf16(self, a_layout, b_layout, M, N, K, A, B):
         """Test helper: C = op(A) op(B) on the tensor cores (A, B CUDA bfloat16)."""
