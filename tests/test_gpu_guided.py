@@ -1,0 +1,26 @@
+"""The surrogate-guided scan end to end at a small scale: what the trained
+network gains over the plain Monte Carlo method without it.
+
+On a 128 x 128 grid of (F, b) of the dichotomous model (400 averaged periods),
+the guided map -- network predictions where the calibrated rule trusts them,
+Monte Carlo re-runs elsewhere -- must reproduce plain Monte Carlo at a random
+sample of grid points within |d<v>| <= 0.01, while spending fewer path-steps
+(labels and re-runs together) than the plain map of the grid.
+"""
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_guided_scan_small_grid():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import guided
+    r = guided.guided_dichot_scan(nx=128, ny=128, n_label=4096, label_paths=2048, rerun_paths=4096,
+                                  transient=20, periods=400, n_valid=1024, steps=6000,
+                                  log=lambda *a: None)
+    assert r["validation_frac_within_0.01"] >= 0.995, r
+    assert r["validation_max_abs_err"] <= 0.02, r
+    assert r["flagged_fraction"] < 0.3, r
+    assert r["ratio_plain_over_guided_total"] > 2.0, r
