@@ -1,0 +1,56 @@
+"""Small, self-contained launches for profiling the engine's kernels.
+
+  python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800
+  python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576
+  python -m paper_1409_4923_gb300.profile_cases scan --points 256
+
+Each case runs its launch twice (a warm-up and the one to capture) and
+prints a checksum, so `ncu -s 1 -c 1 -k <kernel>` captures a warm launch.
+"""
+import argparse
+import sys
+
+
+def main():
+    import numpy as np
+    import torch
+    from . import engine as E, workloads as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["point", "mlp", "scan"])
+    ap.add_argument("workload", nargs="?", default="dichot_2p20")
+    ap.add_argument("--paths", type=int, default=1 << 20)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--rows", type=int, default=1 << 20)
+    ap.add_argument("--points", type=int, default=256)
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    if a.case == "point":
+        spec = W.run_spec(a.workload)
+        eng = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"])
+        for _ in range(2):
+            eng.run(a.paths, spec["dt"], 0, a.steps)
+            print("mean_v", eng.stats()["mean_v"])
+        eng.close()
+    elif a.case == "mlp":
+        from . import surrogate as S
+        rng = np.random.default_rng(0)
+        x = torch.from_numpy(rng.uniform(0.5, 1.5, (a.rows, 7)).astype(np.float32)).cuda()
+        net = S.Surrogate(0)
+        for _ in range(2):
+            y = net.forward(x)
+            torch.cuda.synchronize()
+            print("checksum", float(y.double().sum()))
+        net.close()
+    else:
+        pts = W.scan_64x64()[:a.points]
+        eng = E.Engine(0, E.make_params(**pts[0]["params"]), seed=0)
+        arg = [dict(p, params=E.make_params(**p["params"]), n_avg=min(p["n_avg"], a.steps)) for p in pts]
+        for _ in range(2):
+            res = eng.scan(arg)
+            print("mean_v[0]", res[0]["mean_v"])
+        eng.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
