@@ -128,6 +128,23 @@ def _dist():
     return world, rank, local
 
 
+def reduce_max_over_ranks(x, device=None):
+    """Max of a float over the ranks of the default process group (the slowest
+    rank's time); returns x unchanged without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, world, steps, t_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return float(units_per_rank) * world * steps / t_max
+
+
 def run_engine(args):
     import torch
     import torch.distributed as dist
@@ -172,11 +189,7 @@ def run_engine(args):
         dist.barrier()
     torch.cuda.synchronize()
     times = [a.elapsed_time(b) / 1e3 for a, b in evs]
-    t_total = sum(times)
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = reduce_max_over_ranks(sum(times), device="cuda")
     clocks = clk.summary()
 
     # end to end through the public API with host buffers: create (parameters
@@ -191,14 +204,10 @@ def run_engine(args):
         e.stats()
         e.close()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = statistics.median(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = reduce_max_over_ranks(statistics.median(e2e_times), device="cuda")
 
     units = float(paths) * steps_per_path
-    value = units * world * args.steps / t_total
+    value = weak_scaling_value(units, world, args.steps, t_total)
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", DEFAULT_SM_MHZ))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
