@@ -96,24 +96,30 @@ static double drive(const orc_ctx* c, double t)
 
 typedef struct { const orc_ctx* c; uint32_t w[4]; uint64_t idx_cached; int have; } gauss_gen;
 
-/* Algorithm 2 (three-point law, Eq. 25) or Gaussian increments. */
+/* Algorithm 2 (three-point law, Eq. 25) or Gaussian increments.
+ * Three-point law: steps 4i..4i+3 share word i & 3 of Philox index n >> 4;
+ * step 4i+k uses r_k = 6^k r_0 mod 2^32, i.e. the uniform phi_k = r_k 2^-32 is
+ * frac(6^k phi_0), and Algorithm 2 compares it with 1/6 and 1/3. */
 static double gauss_step(gauss_gen* g, uint64_t n)
 {
     const orc_ctx* c = g->c;
-    uint64_t idx = n >> 2;
+    const int normal = (c->p.noise & ORC_GAUSS_NORMAL) != 0;
+    uint64_t idx = normal ? (n >> 2) : (n >> 4);
     if (!g->have || g->idx_cached != idx) {
         orc_stream_words(c->seed, TAG_GAUSS, c->p.point, c->path, idx, g->w);
         g->idx_cached = idx;
         g->have = 1;
     }
-    if (c->p.noise & ORC_GAUSS_NORMAL) {
+    if (normal) {
         unsigned pair = (unsigned)(n & 3u) >> 1;
         double R = sqrt(-2.0 * log(1.0 - phi24(g->w[2 * pair])));
         double T = TWO_PI * phi24(g->w[2 * pair + 1]);
         double N = (n & 1u) ? R * sin(T) : R * cos(T);
         return c->G * sqrt(c->dt) * N;
     }
-    double phi = (double)g->w[n & 3u] * (1.0 / 4294967296.0);
+    uint32_t r = g->w[(n >> 2) & 3u];
+    for (unsigned k = 0; k < (unsigned)(n & 3u); ++k) r *= 6u;     /* mod 2^32 */
+    double phi = (double)r * (1.0 / 4294967296.0);
     double step = c->G * sqrt(3.0 * c->dt);
     if (phi <= 1.0 / 6.0) return -step;
     if (phi <= 1.0 / 3.0) return step;

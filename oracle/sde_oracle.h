@@ -33,12 +33,13 @@
  *   INIT  idx 0: x0 = x0_lo + (x0_hi - x0_lo) phi(w0)
  *                v0 = v0_lo + (v0_hi - v0_lo) phi(w1)
  *                d0 = 1 (state F_b) iff phi(w2) < mu_a / (mu_a + mu_b)
- *   GAUSS step n: idx n >> 2, word n & 3 = r
- *         three-point (Alg. 2): -c if r 2^-32 <= 1/6, +c if <= 1/3, else 0,
- *                               c = G sqrt(3 dt)
- *         Gaussian: words (0,1) serve steps 4i, 4i+1 and words (2,3) steps
- *               4i+2, 4i+3; R = sqrt(-2 ln u(first)), T = 2 pi phi(second);
- *               even step R cos T, odd step R sin T; increment G sqrt(dt) N
+ *   GAUSS three-point (Alg. 2): step n uses word (n >> 2) & 3 of idx n >> 4,
+ *         r = 6^(n & 3) word mod 2^32; -c if r 2^-32 <= 1/6, +c if <= 1/3,
+ *         else 0, c = G sqrt(3 dt)
+ *   GAUSS Gaussian: idx n >> 2; words (0,1) serve steps 4i, 4i+1 and words
+ *         (2,3) steps 4i+2, 4i+3; R = sqrt(-2 ln u(first)), T = 2 pi
+ *         phi(second); even step R cos T, odd step R sin T; increment
+ *         G sqrt(dt) N
  *   POIS event j (j = 0 is the initial countdown): idx j >> 1, words
  *         2(j&1) and 2(j&1)+1:  wait_j = floor(-ln u(wa) / (lambda dt)),
  *         z_j = -zeta ln u(wb)

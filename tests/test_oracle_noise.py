@@ -107,3 +107,26 @@ def test_dichotomous_process(orc):
     # mean sojourn in -F_a is 1 / qa steps
     sw = np.diff(np.flatnonzero(np.diff((g[0] == Fb).astype(np.int8)) != 0))
     assert len(sw) > 100
+
+
+def test_three_point_steps_sharing_a_word_are_independent(orc):
+    """Four consecutive steps share one Philox word (r, 6r, 36r, 216r mod 2^32):
+    the 3 x 3 joint frequencies of each step and the next match the product
+    law (1/6, 1/6, 2/3)^2, and so do steps 4 apart (different words)."""
+    Q, dt = 0.5, 0.01
+    p = orc.make_params(Q=Q, noise=orc.GAUSS)
+    x = _seq(orc, 1, orc.OVERDAMPED_WASHBOARD, p, 13, 40, dt, 16000)
+    c = math.sqrt(2 * Q) * math.sqrt(3 * dt)
+    cls = np.where(x < 0, 0, np.where(x > 0, 1, 2))
+    probs = np.array([1 / 6, 1 / 6, 2 / 3])
+    for lag in (1, 2, 3, 4):
+        for k in range(4):                       # position within the word
+            a = cls[:, k:-lag:4] if lag < 4 else cls[:, k::4][:, :-1]
+            b = cls[:, k + lag::4][:, :a.shape[1]]
+            a, b = a.ravel()[:b.size], b.ravel()
+            obs = np.zeros((3, 3))
+            np.add.at(obs, (a, b), 1)
+            exp = np.outer(probs, probs) * a.size
+            chi2 = ((obs - exp) ** 2 / exp).sum()
+            assert chi2 < 26.1, (lag, k, chi2)   # 8 dof, p = 0.001
+    assert abs(np.abs(x[x != 0]).mean() - c) < 1e-15
