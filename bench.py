@@ -36,13 +36,14 @@ UNIT = "path-steps/s"
 #   Algorithm 1 on (x, v): 3 drift evaluations x (cos argument 1, SFU cos 1,
 #   force FMA 1, damping FMA 1) = 12, state updates and trapezoid sums 10,
 #   fold of x (scale, round, subtract, count) 4, window sums of v, v^2 2 -> 28
-#   Algorithm 2: one Philox4x32-10 word (10 rounds x 4 ops / 4 words) 10,
-#   three-point selection (2 compares, 2 selects) 4                     -> 14
+#   Algorithm 2: a quarter of one Philox4x32-10 word (10 rounds x 4 ops /
+#   16 steps) 2.5, three-point selection (2 compares, 2 selects) 4, the
+#   uniform of the next step from the same word (one multiply) 1       ->  7.5
 #   drive a cos(w t) + F: one table value per step                      ->  1
 #   Algorithm 3/4 countdown (decrement, test, add of the increment)     ->  3
 #   event tail: p = 1 - exp(-mu dt) = 0.0127 x (1/4 Philox 10, log 1,
 #   scale 1, floor 1, guard 3, convert 1, state 2 = 19)                 ->  0.24
-ALG_OPS_PER_PATH_STEP = 46.24
+ALG_OPS_PER_PATH_STEP = 39.74
 SM_LANES = 128              # FP32 lanes (= issue slots x 32) per SM
 DEFAULT_SM_MHZ = 2070.0
 

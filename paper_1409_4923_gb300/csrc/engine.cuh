@@ -332,17 +332,23 @@ __device__ __forceinline__ bool chunk_events(PathState& S, const PointConsts& P,
     return fits;
 }
 
-// Gaussian increment for step 4 i + k from the word of its group (Algorithm 2 /
-// Eq. 25 three-point law, or Box-Muller for the Gaussian variant).
+// Three-point increment (Algorithm 2, Eq. 25) from the running word r of the
+// step (phi = r 2^-32), then r <- 6 r mod 2^32 for the next step that shares
+// the word: the uniform of step 4i + k is frac(6^k phi_0).
+__device__ __forceinline__ float three_point(uint32_t& r, const PointConsts& P)
+{
+    float d = r <= 1431655765u ? P.xi_c : 0.0f;        // phi <= 1/3
+    d = r <= 715827882u ? -P.xi_c : d;                 // phi <= 1/6
+    r *= 6u;
+    return d;
+}
+
+// Gaussian increment for step 4 i + k from the word of its group (Box-Muller
+// variant; the three-point law uses three_point).
 template <int GAUSS>
 __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const PointConsts& P)
 {
-    if (GAUSS == kGauss3Point) {
-        const uint32_t r = k == 0u ? w.x : (k == 1u ? w.y : (k == 2u ? w.z : w.w));
-        float d = r <= 1431655765u ? P.xi_c : 0.0f;     // phi <= 1/3
-        d = r <= 715827882u ? -P.xi_c : d;              // phi <= 1/6
-        return d;
-    } else if (GAUSS == kGaussNormal) {
+    if (GAUSS == kGaussNormal) {
         const uint32_t wa = k < 2u ? w.x : w.z;
         const uint32_t wb = k < 2u ? w.y : w.w;
         const float R = sqrtf(-2.0f * __logf(u24(wa)));
@@ -364,7 +370,14 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 {
     for (; n < n_end; ++n) {
         float dxi = 0.0f;
-        if (GAUSS != 0) {
+        if (GAUSS == kGauss3Point) {
+            const uint4 w = stream(K, P.c1_gauss, path, n >> 4);
+            const uint32_t q = (n >> 2) & 3u;
+            uint32_t r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
+            const uint32_t k = n & 3u;
+            r *= k == 0u ? 1u : (k == 1u ? 6u : (k == 2u ? 36u : 216u));
+            dxi = three_point(r, P);
+        } else if (GAUSS == kGaussNormal) {
             const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
             dxi = gauss_inc<GAUSS>(w, n & 3u, P);
         }
@@ -375,10 +388,12 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 
 // One 32-step chunk from n0: 8 groups of 4 steps, the drive of step
 // n0 + 1 + l in lane l (shuffled to every lane per step), jump events from
-// the chunk masks (FAST) or inline.  w holds the Gaussian words of the
-// chunk's first group; each group draws the next group's words while it
-// integrates (so the Philox multiplies interleave with the step arithmetic),
-// and w returns holding those of the group after the chunk.
+// the chunk masks (FAST) or inline.  Gaussian words: the three-point law
+// takes one Philox call per 16-step block (one word per group of 4 steps),
+// the Box-Muller variant one per group.  w holds the words of the chunk's
+// first block (group); each block (group) draws the next one's words while it
+// integrates, so the Philox multiplies interleave with the step arithmetic,
+// and w returns holding those that follow the chunk.
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST>
 __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                             uint32_t path, uint32_t n0, float dch, float& dcur,
@@ -388,14 +403,23 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
     // two groups per iteration unless the Poisson queue doubles the body
     // (measured: the unrolled two-variant Poisson chunk runs 15 % slower)
     constexpr int kGroupUnroll = POIS ? 1 : 2;
+    uint4 wn = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll kGroupUnroll
     for (uint32_t g = 0; g < 8u; ++g) {
-        uint4 wn = make_uint4(0u, 0u, 0u, 0u);
-        if (GAUSS != 0) wn = stream(K, P.c1_gauss, path, (n0 >> 2) + g + 1u);
+        uint32_t r = 0u;
+        if (GAUSS == kGauss3Point) {
+            if ((g & 3u) == 0u) wn = stream(K, P.c1_gauss, path, (n0 >> 4) + (g >> 2) + 1u);
+            const uint32_t q = g & 3u;
+            r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
+        } else if (GAUSS == kGaussNormal) {
+            wn = stream(K, P.c1_gauss, path, (n0 >> 2) + g + 1u);
+        }
 #pragma unroll
         for (uint32_t k = 0; k < 4u; ++k) {
             const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
-            const float dxi = gauss_inc<GAUSS>(w, k, P);
+            float dxi = 0.0f;
+            if (GAUSS == kGauss3Point) dxi = three_point(r, P);
+            else if (GAUSS == kGaussNormal) dxi = gauss_inc<GAUSS>(w, k, P);
             float jump = 0.0f;
             if (POIS) {
                 if (FAST) {
@@ -412,7 +436,7 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
             pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, jump, dcur, dnext);
             dcur = dnext;
         }
-        w = wn;
+        if (GAUSS == kGaussNormal || (GAUSS == kGauss3Point && (g & 3u) == 3u)) w = wn;
         pm >>= 4;
         dm >>= 4;
         if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
@@ -436,7 +460,8 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
     if (n + 32u <= n_end) {
         float dcur = drive_at(n, P);
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (GAUSS != 0) w = stream(K, P.c1_gauss, path, n >> 2);
+        if (GAUSS == kGauss3Point) w = stream(K, P.c1_gauss, path, n >> 4);
+        else if (GAUSS == kGaussNormal) w = stream(K, P.c1_gauss, path, n >> 2);
         uint32_t since_flush = 0u;
         for (; n + 32u <= n_end; n += 32u) {
             const float dch = drive_at(n + 1u + lane, P);
