@@ -70,6 +70,17 @@ int sde_mlp_gradients(sde_mlp* net, const float* x, const float* t, uint64_t M,
 int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M, float lr,
                        float beta1, float beta2, float eps, float* loss_dev);
 
+/* Matrix path of the forward pass's two 256 x 256 layers: 1 (default) the
+ * fifth-generation tensor cores (tcgen05.mma with the FP32 accumulator in
+ * tensor memory, persistent CTAs holding the layer's weights in shared
+ * memory), 0 the warp-level mma.sync kernels that also serve training.
+ * Results agree to FP32 accumulation order. */
+int sde_mlp_set_tensor_path(sde_mlp* net, int use_tcgen05);
+
+/* Wait for the network's stream and report device-side failures: SDE_ETIMEDOUT
+ * if a tensor-core completion wait ran out of its iteration limit. */
+int sde_mlp_sync(sde_mlp* net);
+
 /* Building block exposed for tests: C[M][N] (FP32, device) = op(A) op(B) with
  * BF16 operands on the tensor cores.  a_layout 0: A is [M][K] row-major,
  * 1: A is [K][M]; b_layout 0: B is given as [N][K] (row n holds column n of

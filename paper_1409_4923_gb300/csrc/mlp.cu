@@ -18,6 +18,9 @@
 #include "sde.h"
 #include "sde_mlp.h"
 
+cudaError_t sde_tc_silu_layer(const __nv_bfloat16* A, int M, const __nv_bfloat16* W, const float* bias,
+                              __nv_bfloat16* out, int* error, int sm_count, cudaStream_t st);
+
 namespace {
 
 constexpr int kIn = SDE_MLP_IN, kInPad = 16, kH = SDE_MLP_HIDDEN, kOut = SDE_MLP_OUT, kOutPad = 8;
@@ -373,6 +376,9 @@ struct sde_mlp {
     size_t part_elems = 0;
     double* loss64 = nullptr;
     double* host_loss = nullptr;
+    int use_tc = 1;                  // 256 x 256 inference layers on tcgen05
+    int sm_count = 0;
+    int* tc_error = nullptr;         // device word set by a timed-out tensor-core wait
 };
 
 static std::string g_mlp_error;
@@ -436,6 +442,11 @@ static cudaError_t forward_rows(sde_mlp* n, uint64_t Mp, bool store_pre)
     a.C = store_pre ? n->H[0] : nullptr; a.ldc = kH; a.O = n->A[0]; a.ldo = kH; a.bias = n->w + oB1;
     cudaError_t e = gemm<false, false, EPI_FWD_SILU>(a, 0, n->stream);
     for (int l = 1; l < 3 && e == cudaSuccess; ++l) {
+        if (!store_pre && n->use_tc) {
+            e = sde_tc_silu_layer(n->A[l - 1], M, n->wb + (l == 1 ? oW2 : oW3), n->w + (l == 1 ? oB2 : oB3),
+                                  n->A[l], n->tc_error, n->sm_count, n->stream);
+            continue;
+        }
         GemmArgs b{};
         b.M = M; b.N = kH; b.K = kH; b.A = n->A[l - 1]; b.lda = kH;
         b.B = n->wb + (l == 1 ? oW2 : oW3); b.ldb = kH;
@@ -528,6 +539,13 @@ int sde_mlp_create(sde_mlp** out, uint64_t seed, void* cuda_stream)
     if (e == cudaSuccess) e = cudaMalloc(&n->m2, P * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->maps, 32 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->loss64, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&n->tc_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(n->tc_error, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&n->host_loss, sizeof(double));
     if (e != cudaSuccess) {
         mfail(nullptr, SDE_ECUDA, std::string("sde_mlp_create: ") + cudaGetErrorString(e));
@@ -695,6 +713,23 @@ int sde_mlp_gemm_bf16(sde_mlp* n, int a_layout, int b_layout, uint32_t M, uint32
     return SDE_OK;
 }
 
+int sde_mlp_set_tensor_path(sde_mlp* n, int use_tcgen05)
+{
+    if (!n || (use_tcgen05 != 0 && use_tcgen05 != 1)) return SDE_EINVAL;
+    n->use_tc = use_tcgen05;
+    return SDE_OK;
+}
+
+int sde_mlp_sync(sde_mlp* n)
+{
+    if (!n) return SDE_EINVAL;
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream));
+    int err = 0;
+    MLP_CUDA(n, cudaMemcpy(&err, n->tc_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return mfail(n, SDE_ETIMEDOUT, "a tensor-core completion wait ran out (mbarrier not signalled)");
+    return SDE_OK;
+}
+
 int sde_guided_flags(sde_mlp* n, const float* v1, const float* v2, const float* lse, uint32_t nx,
                      uint32_t ny, float kappa, float r0, float se_scale, float tol, float se_tol, uint8_t* flags,
                      uint32_t* count)
@@ -713,7 +748,7 @@ void sde_mlp_destroy(sde_mlp* n)
     if (n->stream || n->own_stream) cudaStreamSynchronize(n->stream);
     free_acts(n);
     cudaFree(n->w); cudaFree(n->wb); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2);
-    cudaFree(n->maps); cudaFree(n->loss64);
+    cudaFree(n->maps); cudaFree(n->loss64); cudaFree(n->tc_error);
     if (n->host_loss) cudaFreeHost(n->host_loss);
     if (n->own_stream) cudaStreamDestroy(n->stream);
     delete n;

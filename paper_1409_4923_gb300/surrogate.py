@@ -36,6 +36,8 @@ def _lib():
                                                  P, ctypes.c_uint32, P, ctypes.c_uint32]),
             "sde_guided_flags": (ctypes.c_int, [P, P, P, P, ctypes.c_uint32, ctypes.c_uint32, f, f, f,
                                                 f, f, P, P]),
+            "sde_mlp_set_tensor_path": (ctypes.c_int, [P, ctypes.c_int]),
+            "sde_mlp_sync": (ctypes.c_int, [P]),
             "sde_mlp_destroy": (None, [P]),
             "sde_mlp_last_error": (ctypes.c_char_p, [P]),
         }
@@ -81,6 +83,14 @@ class Surrogate:
         self._maps = (a, int(log_mask))
         self._check(self._L.sde_mlp_set_maps(self._net, a[0].ctypes.data, a[1].ctypes.data,
                                              int(log_mask), a[2].ctypes.data, a[3].ctypes.data))
+
+    def set_tensor_path(self, use_tcgen05):
+        """1: the 256 x 256 forward layers on tcgen05 (default); 0: mma.sync."""
+        self._check(self._L.sde_mlp_set_tensor_path(self._net, int(use_tcgen05)))
+
+    def sync(self):
+        """Wait for the stream; raises if a tensor-core wait ran out."""
+        self._check(self._L.sde_mlp_sync(self._net))
 
     def get_params(self):
         out = np.zeros(NPARAMS, dtype=np.float32)

@@ -167,3 +167,33 @@ def test_training_fits_a_smooth_function(S):
     assert hist[-50:].mean() < 0.05 * hist[:50].mean()
     rmse = np.sqrt(np.mean((y - t) ** 2, axis=0)) / t.std(0)
     assert np.all(rmse < 0.15), rmse
+
+
+def test_tcgen05_forward_matches_mma_path_and_oracle(S):
+    """The 256 x 256 layers on tcgen05 (FP32 accumulator in tensor memory)
+    against the mma.sync kernels and the FP64 oracle, over a row count that
+    spans two 65536-row chunks and ends in a ragged 128-row tile."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 9)
+    rng = np.random.default_rng(10)
+    M = 65536 + 1000 + 37
+    x = _raw_inputs(rng, M)
+    X = torch.from_numpy(x.astype(np.float32)).cuda()
+    try:
+        net.set_tensor_path(1)
+        y_tc = net.forward(X)
+        net.sync()
+        net.set_tensor_path(0)
+        y_mma = net.forward(X)
+        net.sync()
+        y_tc, y_mma = y_tc.cpu().numpy(), y_mma.cpu().numpy()
+    finally:
+        net.close()
+    rms = np.sqrt(np.mean(((y_mma - osh) / osc) ** 2, axis=0))
+    d = np.abs(y_tc - y_mma) / osc / rms
+    assert np.isfinite(y_tc).all() and d.max() < 0.01, d.max()
+    sel = np.concatenate([np.arange(300), np.arange(M - 300, M)])
+    xp = omlp.input_map(x[sel].astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    yp, _ = omlp.forward(bf16_round(p), xp)
+    err = np.abs(y_tc[sel] - (yp * osc + osh)) / osc / np.sqrt(np.mean(yp ** 2, axis=0))
+    assert err.max() < 0.03, err.max()
