@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kIn = SDE_MLP_IN, kInPad = 16, kH = SDE_MLP_HIDDEN, kOut = SDE_MLP_OUT, kOutPad = 8;
 constexpr uint64_t kMaxBatch = 65536;
+constexpr uint64_t kMaxForwardChunk = 1u << 20;
 constexpr int kSplitRows = 256;        // batch rows per split of the weight-gradient GEMMs
 
 // Offsets in the flat parameter vector.
@@ -632,7 +633,9 @@ int sde_mlp_get_params(sde_mlp* n, float* host)
 int sde_mlp_forward(sde_mlp* n, const float* x, uint64_t M, float* y)
 {
     if (!n || !x || !y || M == 0) return n ? mfail(n, SDE_EINVAL, "bad forward arguments") : SDE_EINVAL;
-    const uint64_t chunk = kMaxBatch;
+    // the tensor-core layers keep their weights resident per CTA: large chunks
+    // amortise the weight loads
+    const uint64_t chunk = n->use_tc ? kMaxForwardChunk : kMaxBatch;
     int rc = ensure_acts(n, pad64(M < chunk ? M : chunk), false);
     if (rc) return rc;
     for (uint64_t r0 = 0; r0 < M; r0 += chunk) {

@@ -1,13 +1,16 @@
 // mlp_tc.cu -- 256 x 256 layers of the surrogate network on the fifth-generation
 // tensor cores (tcgen05): out[M][256] = SiLU(A[M][256] W^T + b) in BF16.
 //
-// One persistent CTA of 128 threads per SM.  The CTA copies W (256 x 256 BF16,
+// One persistent CTA of 256 threads per SM.  The CTA copies W (256 x 256 BF16,
 // 128 KB) into shared memory once, in the 128-byte-swizzled K-major layout the
 // tensor core reads, and then walks 128-row tiles of A: the tile is staged in
-// the same layout (64 KB), one elected thread issues the 16 MMAs of K = 256
-// (tcgen05.mma kind::f16, M = 128, N = 256, FP32 accumulator in TMEM) and
-// commits them to an mbarrier, and each warp reads its 32 TMEM lanes (its 32
-// rows) back with tcgen05.ld for the bias + SiLU epilogue.
+// the same layout (64 KB, cp.async), one elected thread issues the 16 MMAs of
+// K = 256 (tcgen05.mma kind::f16, M = 128, N = 256, FP32 accumulator in TMEM)
+// and commits them to an mbarrier, and each warp reads 32 TMEM lanes (32 rows)
+// of one half of the columns back with tcgen05.ld for the bias + SiLU
+// epilogue (a warp may read the lane quarter of its index modulo 4).  As soon as the
+// MMAs of a tile complete, the copy of the next tile starts, so it overlaps
+// the epilogue.
 //
 // Every wait is bounded: if an mbarrier phase does not complete within the
 // iteration limit the kernel records an error word, stops, releases its TMEM
@@ -28,7 +31,8 @@ constexpr int kBRegion = kN * 128;    // bytes of one K-block of W   (32 KB)
 constexpr int kARegion = kRows * 128; // bytes of one K-block of A   (16 KB)
 constexpr int kBBytes = kKBlocks * kBRegion;   // 128 KB
 constexpr int kABytes = kKBlocks * kARegion;   //  64 KB
-constexpr int kSmemBytes = kBBytes + kABytes + 64 + 1024;   // + barrier, TMEM slot, alignment
+constexpr int kThreads = 256;        // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., column half w / 4
+constexpr int kSmemBytes = kBBytes + kABytes + 64 + kN * 4 + 1024;   // + barrier, TMEM slot, bias, alignment
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -50,7 +54,23 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr)
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
 
-__device__ __forceinline__ float silu(float x) { return x / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
+
+// Asynchronous copy of the 128-row A tile starting at row r0 into the swizzled
+// layout (rows past M are zero-filled by a zero source size).
+__device__ __forceinline__ void load_tile_async(const __nv_bfloat16* __restrict__ A, int M, int r0,
+                                                uint32_t sA_a, uint32_t tid)
+{
+    for (uint32_t i = tid; i < (uint32_t)kRows * (kK / 8); i += (uint32_t)kThreads) {
+        const uint32_t r = i / (kK / 8), c = i % (kK / 8);
+        const bool in = r0 + (int)r < M;
+        const __nv_bfloat16* src = A + (in ? (size_t)(r0 + r) * kK + c * 8u : 0);
+        const uint32_t dst = sA_a + (c >> 3) * kARegion + sw128(r, c & 7u);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                     :: "r"(dst), "l"(src), "r"(in ? 16u : 0u) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase)
 {
@@ -63,7 +83,7 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase)
     return false;
 }
 
-__global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat16* __restrict__ A, int M,
+__global__ void __launch_bounds__(kThreads, 1) silu_layer_tc_kernel(const __nv_bfloat16* __restrict__ A, int M,
                                                                const __nv_bfloat16* __restrict__ W,
                                                                const float* __restrict__ bias,
                                                                __nv_bfloat16* __restrict__ out,
@@ -77,6 +97,7 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
     uint8_t* sA = base + kBBytes;
     uint64_t* mbar = (uint64_t*)(base + kBBytes + kABytes);
     uint32_t* tslot = (uint32_t*)(base + kBBytes + kABytes + 16);
+    float* sbias = (float*)(base + kBBytes + kABytes + 64);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t mbar_a = smem_addr(mbar);
 
@@ -86,8 +107,9 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
+    for (uint32_t i = tid; i < (uint32_t)kN; i += (uint32_t)kThreads) sbias[i] = bias[i];
     // W -> shared memory (256 rows x 32 chunks of 16 bytes)
-    for (uint32_t i = tid; i < (uint32_t)kN * (kK / 8); i += 128u) {
+    for (uint32_t i = tid; i < (uint32_t)kN * (kK / 8); i += (uint32_t)kThreads) {
         const uint32_t n = i / (kK / 8), c = i % (kK / 8);
         const uint4 v = *(const uint4*)(W + (size_t)n * kK + c * 8u);
         *(uint4*)(sB + (c >> 3) * kBRegion + sw128(n, c & 7u)) = v;
@@ -102,15 +124,12 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
     uint32_t phase = 0;
     bool ok = true;
     const int tiles = (M + kRows - 1) / kRows;
-    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    int t = blockIdx.x;
+    if (t < tiles) load_tile_async(A, M, t * kRows, sA_a, tid);
+    for (; t < tiles && ok; t += gridDim.x) {
         const int r0 = t * kRows;
-        // A tile -> shared memory (128 rows x 32 chunks), rows past M zero
-        for (uint32_t i = tid; i < (uint32_t)kRows * (kK / 8); i += 128u) {
-            const uint32_t r = i / (kK / 8), c = i % (kK / 8);
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (r0 + (int)r < M) v = *(const uint4*)(A + (size_t)(r0 + r) * kK + c * 8u);
-            *(uint4*)(sA + (c >> 3) * kARegion + sw128(r, c & 7u)) = v;
-        }
+        // the tile is in shared memory: make it visible to the tensor core
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -133,11 +152,14 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
         ok = __syncthreads_and(mine) != 0;          // one decision for the whole block
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the MMAs have read the tile: fetch the next one during the epilogue
+        if (ok && t + (int)gridDim.x < tiles) load_tile_async(A, M, (t + gridDim.x) * kRows, sA_a, tid);
         if (ok) {
-            const int row = r0 + (int)(warp * 32u + lane);
-            const uint32_t taddr = tmem + ((warp * 32u) << 16);
+            const uint32_t quarter = warp & 3u, half = warp >> 2;
+            const int row = r0 + (int)(quarter * 32u + lane);
+            const uint32_t taddr = tmem + ((quarter * 32u) << 16);
 #pragma unroll 1
-            for (uint32_t cb = 0; cb < (uint32_t)kN; cb += 32u) {
+            for (uint32_t cb = half * (kN / 2); cb < (half + 1u) * (kN / 2); cb += 32u) {
                 uint32_t v[32];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -154,8 +176,8 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
                     uint32_t packed[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float a = silu(__uint_as_float(v[2 * j]) + bias[cb + 2 * j]);
-                        const float b = silu(__uint_as_float(v[2 * j + 1]) + bias[cb + 2 * j + 1]);
+                        const float a = silu(__uint_as_float(v[2 * j]) + sbias[cb + 2 * j]);
+                        const float b = silu(__uint_as_float(v[2 * j + 1]) + sbias[cb + 2 * j + 1]);
                         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
                         packed[j] = *(const uint32_t*)&h;
                     }
@@ -172,6 +194,7 @@ __global__ void __launch_bounds__(128, 1) silu_layer_tc_kernel(const __nv_bfloat
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols) : "memory");
@@ -192,6 +215,6 @@ cudaError_t sde_tc_silu_layer(const __nv_bfloat16* A, int M, const __nv_bfloat16
     }
     const int tiles = (M + sde_tc::kRows - 1) / sde_tc::kRows;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    sde_tc::silu_layer_tc_kernel<<<grid, 128, sde_tc::kSmemBytes, st>>>(A, M, W, bias, out, error);
+    sde_tc::silu_layer_tc_kernel<<<grid, sde_tc::kThreads, sde_tc::kSmemBytes, st>>>(A, M, W, bias, out, error);
     return cudaGetLastError();
 }

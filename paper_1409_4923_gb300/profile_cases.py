@@ -1,7 +1,7 @@
 """Small, self-contained launches for profiling the engine's kernels.
 
   python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800
-  python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576
+  python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576 --path 1
   python -m paper_1409_4923_gb300.profile_cases scan --points 256
 
 Each case runs its launch twice (a warm-up and the one to capture) and
@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--steps", type=int, default=800)
     ap.add_argument("--rows", type=int, default=1 << 20)
     ap.add_argument("--points", type=int, default=256)
+    ap.add_argument("--path", type=int, default=1, help="mlp: 1 tcgen05, 0 mma.sync")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.case == "point":
@@ -36,9 +37,10 @@ def main():
         rng = np.random.default_rng(0)
         x = torch.from_numpy(rng.uniform(0.5, 1.5, (a.rows, 7)).astype(np.float32)).cuda()
         net = S.Surrogate(0)
+        net.set_tensor_path(a.path)
         for _ in range(2):
             y = net.forward(x)
-            torch.cuda.synchronize()
+            net.sync()
             print("checksum", float(y.double().sum()))
         net.close()
     else:
