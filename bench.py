@@ -160,8 +160,15 @@ def run_engine(args):
     n_tr, n_avg = spec["n_transient"], spec["n_avg"]
     steps_per_path = n_tr + n_avg
     stream = torch.cuda.Stream()
-    eng = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
-                   stream=stream)
+    prm = E.make_params(**spec["params"])
+    shape = (128, 0)
+    if not args.no_autotune:
+        from paper_1409_4923_gb300 import autotune
+        b, g, _ = autotune.tune(spec["model"], prm, dt, paths, n_probe_steps=2048,
+                                seed=spec["seed"] + rank, stream=stream)
+        shape = (b, g)
+    eng = E.Engine(spec["model"], prm, seed=spec["seed"] + rank, stream=stream)
+    eng.set_tuning(*shape)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
 
     def one_step():
@@ -201,6 +208,7 @@ def run_engine(args):
         t0 = time.perf_counter()
         e = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
                      stream=stream)
+        e.set_tuning(*shape)
         e.run(paths, dt, n_tr, n_avg)
         e.stats()
         e.close()
@@ -229,7 +237,9 @@ def run_engine(args):
                                                         else "poissonian"),
                    "parallelism": "paths sharded per GPU" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB device write) between timed steps",
-                   "path_arith": "fp32", "accumulators": "fp64"},
+                   "path_arith": "fp32", "accumulators": "fp64",
+                   "launch_shape": {"block_threads": shape[0], "grid_blocks": shape[1] or "persistent",
+                                    "chosen_by": "fixed" if args.no_autotune else "autotuner"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops,
                      "unit": "Top/s (lane ops)", "frac": achieved / peak_tops,
                      "traffic": traffic,
@@ -322,6 +332,8 @@ def main():
     ap.add_argument("--workload", default="dichot_2p20", choices=["dichot_2p20", "poisson_1024"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default launch shape instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

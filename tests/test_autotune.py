@@ -1,0 +1,56 @@
+"""The launch-shape autotuner: selection, cache keys and the cache file (CPU),
+and one real tuning on the GPU whose chosen shape reproduces the default's
+results bit for bit."""
+import json
+
+import pytest
+
+from paper_1409_4923_gb300 import autotune as AT
+
+
+def test_choose_picks_the_fastest_and_keeps_the_first_on_ties():
+    t = {(128, 0): 1.0, (64, 0): 0.8, (32, 152): 0.8, (96, 304): 1.2}
+    assert AT.choose(t) == (64, 0)
+    assert AT.choose({(128, 0): 1.0, (64, 0): 1.0}) == (128, 0)
+
+
+def test_candidates_and_keys():
+    c = AT.candidates(152)
+    assert (128, 0) in c and (32, 608) in c and len(c) == len(AT.BLOCKS) * len(AT.GRID_MULTIPLES)
+    assert AT.size_class(1 << 20) == 10 and AT.size_class(1) == 0
+    assert AT.key("GB300", 0, 5, 1 << 20) != AT.key("GB300", 0, 6, 1 << 20)
+    assert AT.key("GB300", 0, 5, 1 << 20) == AT.key("GB300", 0, 5, (1 << 20) + 5)
+
+
+def test_cache_round_trip(tmp_path):
+    p = str(tmp_path / "sub" / "tune.json")
+    AT._store(p, {"k": {"block": 64, "grid": 0}})
+    assert AT._load(p) == {"k": {"block": 64, "grid": 0}}
+    assert AT._load(str(tmp_path / "missing.json")) == {}
+    with open(p, "w") as f:
+        f.write("{broken")
+    assert AT._load(p) == {}
+
+
+@pytest.mark.gpu
+def test_tune_on_gpu(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import engine as E, workloads as W
+    spec = W.run_spec("dichot_2p20")
+    prm = E.make_params(**spec["params"])
+    cache = str(tmp_path / "tune.json")
+    b, g, t = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, n_probe_steps=512, cache=cache)
+    assert (b, g) in t and len(t) == len(AT.BLOCKS) * len(AT.GRID_MULTIPLES)
+    assert json.load(open(cache))
+    b2, g2, t2 = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, cache=cache)
+    assert (b2, g2) == (b, g) and t2 is None
+    sums = []
+    for shape in ((128, 0), (b, g)):
+        eng = E.Engine(spec["model"], prm, seed=0)
+        eng.set_tuning(*shape)
+        eng.run(5000, spec["dt"], 100, 700)
+        sums.append(eng.stats()["sums"])
+        eng.close()
+    assert sums[0] == sums[1]
