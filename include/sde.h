@@ -24,9 +24,10 @@
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit seed,
  * counter = (index_lo, tag << 30 | point, path, index_hi); tag 0 initial
- * state, 1 Gaussian (word n & 3 of index n >> 2 serves step n), 2 Poisson
- * (event j: words 2(j&1), 2(j&1)+1 of index j >> 1), 3 dichotomous (event j:
- * word j & 3 of index j >> 2).  Uniforms are phi = (w >> 8) 2^-24 in [0,1) and
+ * state, 1 Gaussian (three-point law: word (n >> 2) & 3 of index n >> 4,
+ * multiplied by 6^(n & 3) modulo 2^32, serves step n; Gaussian increments:
+ * words of index n >> 2), 2 Poisson (event j: words 2(j&1), 2(j&1)+1 of index
+ * j >> 1), 3 dichotomous (event j: word j & 3 of index j >> 2).  Uniforms are phi = (w >> 8) 2^-24 in [0,1) and
  * u = 1 - phi in (0,1].  Results are a pure function of (model, parameters,
  * seed, path count, dt, step counts); they do not depend on the launch shape.
  *
