@@ -158,6 +158,67 @@ typedef struct {
 int sde_scan(sde_ctx* ctx, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out,
              double deadline_ms);
 
+/* Continue the last sde_scan of this context after it returned
+ * SDE_ETIMEDOUT: the work items that it did not start run now, under a fresh
+ * deadline_ms (0 = none); the items it finished are kept.  Each item's result
+ * depends only on its point and paths, so the final statistics equal those of
+ * an uninterrupted scan bit for bit.  Writes the statistics of all npts points
+ * of that scan to the host array `out`; synchronises the stream.  Returns
+ * SDE_ETIMEDOUT again if the new deadline also expires (call it again: every
+ * call finishes at least one item per resident warp); SDE_ESTATE if no scan
+ * is pending or another call has used the context's workspace since. */
+int sde_scan_resume(sde_ctx* ctx, sde_stats_t* out, double deadline_ms);
+
+/* Segmented runs and checkpoints.  Algorithm 5 advances the paths by
+ * `samples` steps per kernel call and keeps their state in global memory
+ * between calls (Sec. 5: a kernel run-time limit may forbid one launch for
+ * the whole simulation).  These calls do the same with a state the caller can
+ * also save to host memory and restore in another context or process.  The
+ * random numbers are counter-based, so a path's state is its coordinates,
+ * period count, window sums and next-event counters; no generator state is
+ * saved. */
+
+/* Start a segmented run of the context's current model, parameters and seed;
+ * paths, dt, n_transient, n_avg as sde_run.  Allocates the saved states (84
+ * bytes per path, path count rounded up to 32) on the device and enqueues
+ * nothing.  The run keeps those parameters and that seed: sde_set_params
+ * does not change a run in progress.  Replaces any earlier segmented run. */
+int sde_begin(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_transient, uint64_t n_avg);
+
+/* Enqueue one segment: every path advances by min(n_steps, steps left)
+ * steps (n_steps = 0: to the end) from its saved state, which is saved again.
+ * The segment that reaches n_transient + n_avg also enqueues the Eq. 31
+ * reduction (sde_stats then returns the run's statistics) and writes the
+ * per-path results to `out` (device arrays as in sde_run_paths; `out` may be
+ * NULL).  When every cut point is a multiple of 32 steps or n_transient, the
+ * results are bit-identical to those of sde_run / sde_run_paths; other cut
+ * points fold x at other steps, which changes FP32 rounding but not the
+ * random events.  Calling it on a complete run enqueues the reduction again.
+ * *n_done (host, may be NULL) receives the steps done after this segment.
+ * Asynchronous.  SDE_ESTATE without sde_begin or sde_restore. */
+int sde_advance(sde_ctx* ctx, uint64_t n_steps, const sde_path_out* out, uint64_t* n_done);
+
+/* Size in bytes of a checkpoint of the current segmented run (host output). */
+int sde_checkpoint_size(sde_ctx* ctx, uint64_t* bytes);
+
+/* Write a checkpoint of the segmented run into the host buffer `buf` of
+ * `bytes` bytes, after waiting for the context's stream: a 224-byte header
+ * (magic "SDECKPT1", format version, model, seed, parameters, dt, paths, step
+ * counts, steps done, FNV-1a 64 checksum of the states) followed by the saved
+ * states in their device layout (structure of arrays).  SDE_EINVAL if bytes is
+ * smaller than sde_checkpoint_size; SDE_ESTATE without a segmented run. */
+int sde_checkpoint(sde_ctx* ctx, void* buf, uint64_t bytes);
+
+/* Make the checkpoint in the host buffer `buf` (`bytes` bytes, not kept) the
+ * context's segmented run, to be continued by sde_advance with the
+ * checkpoint's parameters and seed (the context's own stay in force for
+ * sde_run and sde_scan).  The context's model must match.  Before anything
+ * reaches the device the header, the checksum and every path's event
+ * counters (next event at or after the current step, event index >= 1,
+ * dichotomous state 0 or 1) are checked: SDE_EINVAL on any mismatch.
+ * Synchronises the stream. */
+int sde_restore(sde_ctx* ctx, const void* buf, uint64_t bytes);
+
 /* Reduce `n` device doubles `vals` to {n, sum, sum of squares} with the same
  * FP64 fold the engine uses (pairwise within a warp, Kahan across items).
  * `out3` is a host array of three doubles.  Synchronises the stream. */

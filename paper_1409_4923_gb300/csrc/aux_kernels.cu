@@ -10,6 +10,12 @@ cudaError_t launch_point_m1(bool, bool, int, const PointConsts&, const LaunchCon
                             const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t);
 cudaError_t launch_point_m2(bool, bool, int, const PointConsts&, const LaunchConsts&,
                             const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t);
+#define SDE_SEG_DECL(M) \
+cudaError_t launch_segment_m##M(bool, bool, int, const PointConsts&, const LaunchConsts&, \
+                                const StatePlanes&, uint32_t, uint32_t, const Workspace&, \
+                                const PathOutPtrs&, int, int, int, cudaStream_t);
+SDE_SEG_DECL(0) SDE_SEG_DECL(1) SDE_SEG_DECL(2)
+#undef SDE_SEG_DECL
 int blocks_per_sm_m0(bool, bool, int, int);
 int blocks_per_sm_m1(bool, bool, int, int);
 int blocks_per_sm_m2(bool, bool, int, int);
@@ -22,6 +28,20 @@ cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const Point
     case kModelInertial: return launch_point_m0(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
     case kModelOverdampedWashboard: return launch_point_m1(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
     case kModelPWL: return launch_point_m2(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+                           const LaunchConsts& K, const StatePlanes& M, uint32_t na, uint32_t nb,
+                           const Workspace& ws, const PathOutPtrs& po, int bt, int gb, int sm,
+                           cudaStream_t st)
+{
+    switch (model) {
+    case kModelInertial: return launch_segment_m0(pois, dich, gauss, P, K, M, na, nb, ws, po, bt, gb, sm, st);
+    case kModelOverdampedWashboard:
+        return launch_segment_m1(pois, dich, gauss, P, K, M, na, nb, ws, po, bt, gb, sm, st);
+    case kModelPWL: return launch_segment_m2(pois, dich, gauss, P, K, M, na, nb, ws, po, bt, gb, sm, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -29,6 +29,59 @@ struct ScanGraph {
     cudaGraphExec_t exec = nullptr;
 };
 
+// What sde_scan_resume needs of a scan that ran out of time.
+struct PendingScan {
+    bool pending = false;
+    uint64_t gen = 0;
+    uint32_t npts = 0;
+    uint32_t flags = 0;
+    uint32_t total_items = 0;
+    bool scan_kernel = false;
+    size_t off_counters = 0, off_out5 = 0, off_ranges = 0, off_partials = 0, off_pts = 0,
+           off_items = 0;
+    std::vector<uint64_t> n_avg;
+    std::vector<uint2> ranges;
+    std::vector<PointConsts> P;
+    std::vector<int> gauss;
+};
+
+struct SegmentedRun {
+    bool active = false;
+    sde_params p{};
+    uint64_t seed = 0;
+    uint64_t paths = 0, n_tr = 0, n_avg = 0, n_done = 0;
+    double dt = 0.0;
+    uint32_t items = 0, stride = 0;
+};
+
+// Checkpoint header (host byte order; followed by the saved states).
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t model;
+    uint64_t seed;
+    sde_params p;
+    double dt;
+    uint64_t paths, n_tr, n_avg, n_done;
+    uint32_t stride, bytes_per_path;
+    uint64_t state_bytes;
+    uint64_t checksum;
+};
+static_assert(sizeof(CkptHeader) == 224, "checkpoint header layout");
+constexpr char kCkptMagic[8] = {'S', 'D', 'E', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+// FNV-1a, 64 bit.
+uint64_t fnv1a64(const unsigned char* p, size_t n)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
 }  // namespace
 
 struct sde_ctx {
@@ -55,6 +108,14 @@ struct sde_ctx {
     int grid_blocks = 0;          // 0 = persistent grid from occupancy
     // scan graphs keyed by (npts, n_items, flags, budget)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, ScanGraph> graphs;
+    // bumped by every call that writes the workspace; a timed-out scan can be
+    // resumed only while its workspace is untouched
+    uint64_t ws_gen = 0;
+    PendingScan scan;
+    // segmented run and its saved path states (device)
+    SegmentedRun seg;
+    void* state = nullptr;
+    size_t state_bytes = 0;
 };
 
 static std::string g_create_error;
@@ -201,9 +262,12 @@ LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns)
     return K;
 }
 
-// Cached scan graphs bake workspace and pinned-buffer addresses.
+// Cached scan graphs bake workspace and pinned-buffer addresses and the
+// launch shape; dropped (after the stream drains) when any of them changes.
 static void drop_graphs(sde_ctx* c)
 {
+    if (c->graphs.empty()) return;
+    cudaStreamSynchronize(c->stream);
     for (auto& kv : c->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
@@ -329,6 +393,7 @@ int sde_set_tuning(sde_ctx* c, int block_threads, int grid_blocks)
     if (block_threads < 32 || block_threads > 128 || block_threads % 32)
         return fail(c, SDE_EINVAL, "block_threads must be 32, 64, 96 or 128");
     if (grid_blocks < 0) return fail(c, SDE_EINVAL, "grid_blocks must be >= 0");
+    if (block_threads != c->block_threads || grid_blocks != c->grid_blocks) drop_graphs(c);
     c->block_threads = block_threads;
     c->grid_blocks = grid_blocks;
     return SDE_OK;
@@ -357,6 +422,7 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
     const Layout L = layout(1, items, 0);
     if ((rc = ensure_ws(c, L.total))) return rc;
     if ((rc = ensure_host(c, 64))) return rc;
+    ++c->ws_gen;
     char* base = (char*)c->ws;
     Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
     uint2* ranges = (uint2*)(base + L.off_ranges);
@@ -439,18 +505,23 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
         if (rc) return rc;
     }
     const bool use_scan_kernel = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
-    const size_t extra = align256(sizeof(PointConsts) * npts) + align256(sizeof(uint2) * total_items);
+    const size_t off_items = align256(sizeof(PointConsts) * npts);
+    const size_t off_counters = off_items + align256(sizeof(uint2) * total_items);
+    const size_t extra = off_counters + align256(sizeof(uint32_t) * npts);
     const Layout L = layout(npts, total_items, extra);
     int rc;
     if ((rc = ensure_ws(c, L.total))) return rc;
     const size_t host_need = sizeof(double) * 5 * npts + 64;
     if ((rc = ensure_host(c, host_need))) return rc;
+    c->scan.pending = false;
+    const uint64_t gen = ++c->ws_gen;
     char* base = (char*)c->ws;
     Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
     uint2* d_ranges = (uint2*)(base + L.off_ranges);
     double* d_out5 = (double*)(base + L.off_out5);
     PointConsts* d_pts = (PointConsts*)(base + L.off_extra);
-    uint2* d_items = (uint2*)(base + L.off_extra + align256(sizeof(PointConsts) * npts));
+    uint2* d_items = (uint2*)(base + L.off_extra + off_items);
+    uint32_t* d_counters = (uint32_t*)(base + L.off_extra + off_counters);
     SDE_CUDA(c, cudaMemcpyAsync(d_pts, P.data(), sizeof(PointConsts) * npts, cudaMemcpyHostToDevice, c->stream));
     SDE_CUDA(c, cudaMemcpyAsync(d_items, items.data(), sizeof(uint2) * total_items, cudaMemcpyHostToDevice, c->stream));
     SDE_CUDA(c, cudaMemcpyAsync(d_ranges, ranges.data(), sizeof(uint2) * npts, cudaMemcpyHostToDevice, c->stream));
@@ -491,12 +562,13 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             SDE_CUDA(c, cudaGraphLaunch(it->second.exec, c->stream));
         }
     } else {
-        // other models: one point-kernel launch per point, same fold
+        // other models: one point-kernel launch per point (each with its own
+        // work counter, so that a timed-out scan can resume), same fold
         SDE_CUDA(c, cudaMemsetAsync(base + 4, 0, 4, c->stream));
+        SDE_CUDA(c, cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * npts, c->stream));
         for (uint32_t i = 0; i < npts; ++i) {
             const LaunchConsts K = make_launch(c->seed, ranges[i].y, budget);
-            Workspace wsi{ws.counter, ws.status, ws.partials + 5ull * ranges[i].x};
-            SDE_CUDA(c, cudaMemsetAsync(base, 0, 4, c->stream));
+            Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * ranges[i].x};
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (flags & SDE_NOISE_POISSON) != 0,
                                      (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(pts[i].p), P[i], K, wsi,
@@ -509,7 +581,269 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
     SDE_CUDA(c, cudaStreamSynchronize(c->stream));
     const int32_t status = *h_status;
     for (uint32_t i = 0; i < npts; ++i) fill_stats(h_out + 5ull * i, status, pts[i].n_avg, &out[i]);
-    return status == kStatusOk ? SDE_OK : fail(c, SDE_ETIMEDOUT, "device deadline expired");
+    if (status == kStatusOk) return SDE_OK;
+    PendingScan& S = c->scan;
+    S.pending = true;
+    S.gen = gen;
+    S.npts = npts;
+    S.flags = flags;
+    S.total_items = (uint32_t)total_items;
+    S.scan_kernel = use_scan_kernel;
+    S.off_counters = L.off_extra + off_counters;
+    S.off_out5 = L.off_out5;
+    S.off_ranges = L.off_ranges;
+    S.off_partials = L.off_partials;
+    S.off_pts = L.off_extra;
+    S.off_items = L.off_extra + off_items;
+    S.n_avg.resize(npts);
+    S.gauss.resize(npts);
+    for (uint32_t i = 0; i < npts; ++i) {
+        S.n_avg[i] = pts[i].n_avg;
+        S.gauss[i] = gauss_kind(pts[i].p);
+    }
+    S.ranges = ranges;
+    S.P = P;
+    return fail(c, SDE_ETIMEDOUT, "device deadline expired");
+}
+
+int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)
+{
+    if (!c || !out) return SDE_EINVAL;
+    if (!(deadline_ms >= 0.0) || !std::isfinite(deadline_ms)) return fail(c, SDE_EINVAL, "deadline_ms must be >= 0");
+    PendingScan& S = c->scan;
+    if (!S.pending) return fail(c, SDE_ESTATE, "no timed-out scan to resume");
+    if (S.gen != c->ws_gen) {
+        S.pending = false;
+        return fail(c, SDE_ESTATE, "the scan's workspace was used by another call");
+    }
+    const uint64_t budget = (uint64_t)(deadline_ms * 1e6);
+    char* base = (char*)c->ws;
+    Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + S.off_partials)};
+    double* d_out5 = (double*)(base + S.off_out5);
+    uint2* d_ranges = (uint2*)(base + S.off_ranges);
+    double* h_out = c->host;
+    int32_t* h_status = (int32_t*)(c->host + 5ull * S.npts);
+    // the work counters keep the items already handed out (all of them finished)
+    SDE_CUDA(c, cudaMemsetAsync(ws.status, 0, 4, c->stream));
+    if (S.scan_kernel) {
+        const LaunchConsts K = make_launch(c->seed, S.total_items, budget);
+        SDE_CUDA(c, launch_scan((S.flags & SDE_NOISE_POISSON) != 0, (S.flags & SDE_NOISE_DICHOT) != 0,
+                                (S.flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0,
+                                (const PointConsts*)(base + S.off_pts), (const uint2*)(base + S.off_items),
+                                K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+    } else {
+        uint32_t* d_counters = (uint32_t*)(base + S.off_counters);
+        for (uint32_t i = 0; i < S.npts; ++i) {
+            const LaunchConsts K = make_launch(c->seed, S.ranges[i].y, budget);
+            Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * S.ranges[i].x};
+            PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
+            SDE_CUDA(c, launch_point((int)c->model, (S.flags & SDE_NOISE_POISSON) != 0,
+                                     (S.flags & SDE_NOISE_DICHOT) != 0, S.gauss[i], S.P[i], K, wsi, po,
+                                     c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+        }
+    }
+    SDE_CUDA(c, launch_fold(ws.partials, d_ranges, S.npts, d_out5, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * S.npts, cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int32_t status = *h_status;
+    for (uint32_t i = 0; i < S.npts; ++i) fill_stats(h_out + 5ull * i, status, S.n_avg[i], &out[i]);
+    if (status == kStatusOk) {
+        S.pending = false;
+        return SDE_OK;
+    }
+    return fail(c, SDE_ETIMEDOUT, "device deadline expired");
+}
+
+// ---------------------------------------------------------------- segmented runs
+
+static int ensure_state(sde_ctx* c, size_t bytes)
+{
+    if (bytes <= c->state_bytes) return SDE_OK;
+    if (c->state) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->state);
+        c->state = nullptr;
+        c->state_bytes = 0;
+    }
+    SDE_CUDA(c, cudaMalloc(&c->state, bytes));
+    c->state_bytes = bytes;
+    return SDE_OK;
+}
+
+static uint64_t seg_state_bytes(const SegmentedRun& r)
+{
+    return r.n_done ? (uint64_t)kStateBytesPerPath * r.stride : 0ull;
+}
+
+int sde_begin(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
+{
+    if (!c) return SDE_EINVAL;
+    int rc = validate_run(c, paths, dt, n_tr, n_avg);
+    if (rc) return rc;
+    PointConsts P;
+    if ((rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, 0u, P))) return rc;
+    SegmentedRun r;
+    r.p = c->p;
+    r.seed = c->seed;
+    r.paths = paths;
+    r.dt = dt;
+    r.n_tr = n_tr;
+    r.n_avg = n_avg;
+    r.n_done = 0;
+    r.items = (uint32_t)((paths + 31ull) / 32ull);
+    r.stride = r.items * 32u;
+    if ((rc = ensure_state(c, (size_t)kStateBytesPerPath * r.stride))) return rc;
+    r.active = true;
+    c->seg = r;
+    c->has_run = false;
+    return SDE_OK;
+}
+
+int sde_advance(sde_ctx* c, uint64_t n_steps, const sde_path_out* out, uint64_t* n_done)
+{
+    if (!c) return SDE_EINVAL;
+    SegmentedRun& r = c->seg;
+    if (!r.active) return fail(c, SDE_ESTATE, "sde_advance without sde_begin or sde_restore");
+    const uint64_t total = r.n_tr + r.n_avg;
+    const uint64_t na = r.n_done;
+    const uint64_t nb = (n_steps == 0 || n_steps >= total - na) ? total : na + n_steps;
+    PointConsts P;
+    int rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, 0u, P);
+    if (rc) return rc;
+    const Layout L = layout(1, r.items, 0);
+    if ((rc = ensure_ws(c, L.total))) return rc;
+    if ((rc = ensure_host(c, 64))) return rc;
+    ++c->ws_gen;
+    char* base = (char*)c->ws;
+    Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
+    uint2* ranges = (uint2*)(base + L.off_ranges);
+    double* out5 = (double*)(base + L.off_out5);
+    const bool last = nb == total;
+    SDE_CUDA(c, cudaMemsetAsync(base, 0, 8, c->stream));
+    PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (out && last) po = PathOutPtrs{out->X_f, out->v_f, out->vbar, out->jP, out->jD};
+    const LaunchConsts K = make_launch(r.seed, r.items, 0);
+    const StatePlanes M{(unsigned char*)c->state, r.stride};
+    const uint32_t f = r.p.noise_flags;
+    SDE_CUDA(c, launch_segment((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+                               gauss_kind(r.p), P, K, M, (uint32_t)na, (uint32_t)nb, ws, po,
+                               c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+    if (last) {
+        const uint2 r0 = make_uint2(0u, r.items);
+        SDE_CUDA(c, cudaMemcpyAsync(ranges, &r0, sizeof(r0), cudaMemcpyHostToDevice, c->stream));
+        SDE_CUDA(c, launch_fold(ws.partials, ranges, 1, out5, c->stream));
+        SDE_CUDA(c, cudaMemcpyAsync(c->host, out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDE_CUDA(c, cudaMemcpyAsync(c->host + 5, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        SDE_CUDA(c, cudaEventRecord(c->done, c->stream));
+        c->has_run = true;
+        c->last_paths = r.paths;
+        c->last_n_avg = r.n_avg;
+    }
+    r.n_done = nb;
+    if (n_done) *n_done = nb;
+    return SDE_OK;
+}
+
+int sde_checkpoint_size(sde_ctx* c, uint64_t* bytes)
+{
+    if (!c || !bytes) return SDE_EINVAL;
+    if (!c->seg.active) return fail(c, SDE_ESTATE, "no segmented run");
+    *bytes = sizeof(CkptHeader) + seg_state_bytes(c->seg);
+    return SDE_OK;
+}
+
+int sde_checkpoint(sde_ctx* c, void* buf, uint64_t bytes)
+{
+    if (!c) return SDE_EINVAL;
+    const SegmentedRun& r = c->seg;
+    if (!r.active) return fail(c, SDE_ESTATE, "no segmented run");
+    const uint64_t sb = seg_state_bytes(r);
+    if (!buf || bytes < sizeof(CkptHeader) + sb) return fail(c, SDE_EINVAL, "checkpoint buffer too small");
+    unsigned char* dst = (unsigned char*)buf + sizeof(CkptHeader);
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sb) {
+        SDE_CUDA(c, cudaMemcpyAsync(dst, c->state, sb, cudaMemcpyDeviceToHost, c->stream));
+        SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.model = (uint32_t)c->model;
+    h.seed = r.seed;
+    h.p = r.p;
+    h.dt = r.dt;
+    h.paths = r.paths;
+    h.n_tr = r.n_tr;
+    h.n_avg = r.n_avg;
+    h.n_done = r.n_done;
+    h.stride = r.stride;
+    h.bytes_per_path = kStateBytesPerPath;
+    h.state_bytes = sb;
+    h.checksum = fnv1a64(dst, sb);
+    std::memcpy(buf, &h, sizeof(h));
+    return SDE_OK;
+}
+
+int sde_restore(sde_ctx* c, const void* buf, uint64_t bytes)
+{
+    if (!c) return SDE_EINVAL;
+    if (!buf || bytes < sizeof(CkptHeader)) return fail(c, SDE_EINVAL, "checkpoint too short");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0) return fail(c, SDE_EINVAL, "not a checkpoint");
+    if (h.version != kCkptVersion) return fail(c, SDE_EINVAL, "unknown checkpoint version");
+    if (h.model != (uint32_t)c->model) return fail(c, SDE_EINVAL, "checkpoint of another model");
+    int rc = validate_params(c, c->model, &h.p);
+    if (rc) return rc;
+    if ((rc = validate_run(c, h.paths, h.dt, h.n_tr, h.n_avg))) return rc;
+    SegmentedRun r;
+    r.p = h.p;
+    r.seed = h.seed;
+    r.paths = h.paths;
+    r.dt = h.dt;
+    r.n_tr = h.n_tr;
+    r.n_avg = h.n_avg;
+    r.n_done = h.n_done;
+    r.items = (uint32_t)((h.paths + 31ull) / 32ull);
+    r.stride = r.items * 32u;
+    if (h.n_done > h.n_tr + h.n_avg) return fail(c, SDE_EINVAL, "steps done exceed the run");
+    if (h.stride != r.stride || h.bytes_per_path != kStateBytesPerPath)
+        return fail(c, SDE_EINVAL, "checkpoint state layout mismatch");
+    const uint64_t sb = seg_state_bytes(r);
+    if (h.state_bytes != sb || bytes - sizeof(CkptHeader) < sb)
+        return fail(c, SDE_EINVAL, "checkpoint truncated");
+    const unsigned char* src = (const unsigned char*)buf + sizeof(CkptHeader);
+    if (fnv1a64(src, sb) != h.checksum) return fail(c, SDE_EINVAL, "checkpoint checksum mismatch");
+    PointConsts P;
+    if ((rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, 0u, P))) return rc;
+    if (sb) {
+        // event counters: planes 0 (eP), 1 (JP), 4 (eD), 5 (JD), 6 (dst) of the u32 block
+        const bool pois = (r.p.noise_flags & SDE_NOISE_POISSON) != 0;
+        const bool dich = (r.p.noise_flags & SDE_NOISE_DICHOT) != 0;
+        const unsigned char* u = src + 44ull * r.stride;
+        auto word = [&](int plane, uint32_t i) {
+            uint32_t w;
+            std::memcpy(&w, u + 4ull * ((uint64_t)plane * r.stride + i), 4);
+            return w;
+        };
+        for (uint32_t i = 0; i < r.stride; ++i) {
+            if (pois && (word(0, i) < r.n_done || word(1, i) < 1u))
+                return fail(c, SDE_EINVAL, "checkpoint: invalid Poisson event counter");
+            if (dich && (word(4, i) < r.n_done || word(5, i) < 1u || word(6, i) > 1u))
+                return fail(c, SDE_EINVAL, "checkpoint: invalid dichotomous event counter");
+        }
+    }
+    if ((rc = ensure_state(c, (size_t)kStateBytesPerPath * r.stride))) return rc;
+    if (sb) {
+        SDE_CUDA(c, cudaMemcpyAsync(c->state, src, sb, cudaMemcpyHostToDevice, c->stream));
+        SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    r.active = true;
+    c->seg = r;
+    c->has_run = false;
+    return SDE_OK;
 }
 
 int sde_reduce_f64(sde_ctx* c, const double* vals, uint64_t n, double* out3)
@@ -521,6 +855,7 @@ int sde_reduce_f64(sde_ctx* c, const double* vals, uint64_t n, double* out3)
     int rc;
     if ((rc = ensure_ws(c, L.total))) return rc;
     if ((rc = ensure_host(c, 64))) return rc;
+    ++c->ws_gen;
     char* base = (char*)c->ws;
     double* partials = (double*)(base + L.off_partials);
     uint2* ranges = (uint2*)(base + L.off_ranges);
@@ -545,6 +880,7 @@ int sde_philox_words(sde_ctx* c, const uint32_t* ctr, uint64_t n, uint64_t seed,
     const size_t bytes = align256(16 * n);
     int rc;
     if ((rc = ensure_ws(c, 2 * bytes))) return rc;
+    ++c->ws_gen;
     uint4* d_in = (uint4*)c->ws;
     uint4* d_out = (uint4*)((char*)c->ws + bytes);
     SDE_CUDA(c, cudaMemcpyAsync(d_in, ctr, 16 * n, cudaMemcpyHostToDevice, c->stream));
@@ -561,6 +897,7 @@ void sde_destroy(sde_ctx* c)
     if (c->stream || c->own_stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     if (c->ws) cudaFree(c->ws);
+    if (c->state) cudaFree(c->state);
     if (c->host) cudaFreeHost(c->host);
     if (c->done) cudaEventDestroy(c->done);
     if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -445,8 +445,10 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
 
 // Steps n in [n, n_end): edges one at a time, whole 32-step chunks with the
 // events of each chunk drawn up front.  The FP32 window partials are moved to
-// the FP64 accumulators every 8 chunks (256 steps).  All 32 lanes of the warp
-// must call this together.
+// the FP64 accumulators whenever a chunk ends on a multiple of 256 steps.
+// Chunks and flushes sit at absolute step positions, so a run cut into
+// segments at multiples of 32 steps takes the same arithmetic as one launch.
+// All 32 lanes of the warp must call this together.
 template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                           uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
@@ -462,7 +464,6 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (GAUSS == kGauss3Point) w = stream(K, P.c1_gauss, path, n >> 4);
         else if (GAUSS == kGaussNormal) w = stream(K, P.c1_gauss, path, n >> 2);
-        uint32_t since_flush = 0u;
         for (; n + 32u <= n_end; n += 32u) {
             const float dch = drive_at(n + 1u + lane, P);
             uint32_t pm, dm;
@@ -473,12 +474,11 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
             else
                 chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, false>(S, P, K, path, n, dch, dcur, w, pm,
                                                                   z0, z1, z2, dm);
-            if (ACC && ++since_flush == 8u) {
+            if (ACC && ((n + 32u) & 255u) == 0u) {
                 S.svd += (double)S.sv;
                 S.sv2d += (double)S.sv2;
                 S.sv = 0.0f;
                 S.sv2 = 0.0f;
-                since_flush = 0u;
             }
         }
     }
@@ -521,6 +521,21 @@ struct PathResult {
     uint32_t jP, jD;
 };
 
+// Eq. 31 summand and the path's other results from its final state.
+template <int MODEL, bool POIS, bool DICH>
+__device__ __forceinline__ void finish_path(const PathState& S, const PointConsts& P, PathResult& R)
+{
+    const double dX = ((double)S.kf - (double)S.kf_i) * P.period
+                    + ((double)S.c - (double)S.c_i) * P.coord_to_x;
+    R.X_f = (double)S.kf * P.period + (double)S.c * P.coord_to_x;
+    R.vbar = dX * P.inv_window;
+    R.sum_v = S.svd + (double)S.sv;
+    R.sum_v2 = S.sv2d + (double)S.sv2;
+    R.v_f = S.v;
+    R.jP = POIS ? S.JP - 1u : 0u;     // index of the last event that happened
+    R.jD = DICH ? S.JD - 1u : 0u;
+}
+
 template <int MODEL, bool POIS, bool DICH, int GAUSS>
 __device__ __forceinline__ void simulate_path(const PointConsts& P, const LaunchConsts& K,
                                               uint32_t path, uint32_t lane, PathResult& R)
@@ -533,15 +548,71 @@ __device__ __forceinline__ void simulate_path(const PointConsts& P, const Launch
     S.kf_i = S.kf;
     run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane, P.n_tr,
                                                                  P.n_tr + P.n_avg);
-    const double dX = ((double)S.kf - (double)S.kf_i) * P.period
-                    + ((double)S.c - (double)S.c_i) * P.coord_to_x;
-    R.X_f = (double)S.kf * P.period + (double)S.c * P.coord_to_x;
-    R.vbar = dX * P.inv_window;
-    R.sum_v = S.svd + (double)S.sv;
-    R.sum_v2 = S.sv2d + (double)S.sv2;
-    R.v_f = S.v;
-    R.jP = POIS ? S.JP - 1u : 0u;     // index of the last event that happened
-    R.jD = DICH ? S.JD - 1u : 0u;
+    finish_path<MODEL, POIS, DICH>(S, P, R);
+}
+
+// Steps [na, nb) of a path whose state is at step na: the part of the
+// transient in the segment, the snapshot at t_i if the transient ends in it,
+// then the part of the averaging window.  Cut points at multiples of 32 steps
+// (or at n_transient) give the arithmetic of simulate_path exactly.
+template <int MODEL, bool POIS, bool DICH, int GAUSS>
+__device__ __forceinline__ void advance_path(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                             uint32_t path, uint32_t lane, uint32_t na, uint32_t nb)
+{
+    const uint32_t ntr = P.n_tr;
+    if (na < ntr) run_steps<MODEL, POIS, DICH, GAUSS, false>(S, P, K, path, lane, na, min(nb, ntr));
+    if ((na < ntr && nb >= ntr) || (na == 0u && ntr == 0u)) {
+        if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
+        S.c_i = S.c;
+        S.kf_i = S.kf;
+    }
+    if (nb > ntr)
+        run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane,
+                                                                     max(na, ntr), nb);
+}
+
+// ---------------------------------------------------------------- saved state
+
+// Path states of a segmented run in global memory (Algorithm 5 keeps the
+// state in registers within a launch and in global memory between launches):
+// structure of arrays, `stride` paths per plane (a multiple of 32, so each
+// warp's loads and stores are whole 128-byte lines).  Planes: 2 FP64 (svd,
+// sv2d), then 7 FP32 (c, v, kf, c_i, kf_i, sv, sv2), then 10 u32 (eP, JP, pw2,
+// pw3, eD, JD, dst, dw1, dw2, dw3): 84 bytes per path.
+constexpr uint32_t kStateBytesPerPath = 84u;
+
+struct StatePlanes {
+    unsigned char* base;
+    uint32_t stride;
+    __device__ __forceinline__ double* d(int k) const { return (double*)base + (size_t)k * stride; }
+    __device__ __forceinline__ float* f(int k) const
+    {
+        return (float*)(base + 16ull * stride) + (size_t)k * stride;
+    }
+    __device__ __forceinline__ uint32_t* u(int k) const
+    {
+        return (uint32_t*)(base + 44ull * stride) + (size_t)k * stride;
+    }
+};
+
+__device__ __forceinline__ void load_state(PathState& S, const StatePlanes& M, uint32_t path)
+{
+    S.svd = M.d(0)[path]; S.sv2d = M.d(1)[path];
+    S.c = M.f(0)[path]; S.v = M.f(1)[path]; S.kf = M.f(2)[path];
+    S.c_i = M.f(3)[path]; S.kf_i = M.f(4)[path]; S.sv = M.f(5)[path]; S.sv2 = M.f(6)[path];
+    S.eP = M.u(0)[path]; S.JP = M.u(1)[path]; S.pw2 = M.u(2)[path]; S.pw3 = M.u(3)[path];
+    S.eD = M.u(4)[path]; S.JD = M.u(5)[path]; S.dst = M.u(6)[path];
+    S.dw1 = M.u(7)[path]; S.dw2 = M.u(8)[path]; S.dw3 = M.u(9)[path];
+}
+
+__device__ __forceinline__ void store_state(const PathState& S, const StatePlanes& M, uint32_t path)
+{
+    M.d(0)[path] = S.svd; M.d(1)[path] = S.sv2d;
+    M.f(0)[path] = S.c; M.f(1)[path] = S.v; M.f(2)[path] = S.kf;
+    M.f(3)[path] = S.c_i; M.f(4)[path] = S.kf_i; M.f(5)[path] = S.sv; M.f(6)[path] = S.sv2;
+    M.u(0)[path] = S.eP; M.u(1)[path] = S.JP; M.u(2)[path] = S.pw2; M.u(3)[path] = S.pw3;
+    M.u(4)[path] = S.eD; M.u(5)[path] = S.JD; M.u(6)[path] = S.dst;
+    M.u(7)[path] = S.dw1; M.u(8)[path] = S.dw2; M.u(9)[path] = S.dw3;
 }
 
 // ---------------------------------------------------------------- reductions

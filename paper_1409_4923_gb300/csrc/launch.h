@@ -19,6 +19,14 @@ cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const Point
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                          int block_threads, int grid_blocks, int sm_count, cudaStream_t st);
 
+// One segment [na, nb) of a segmented run over the saved path states M
+// (na == 0 draws the initial states; nb == n_transient + n_avg also writes
+// the item partials and per-path results).
+cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+                           const LaunchConsts& K, const StatePlanes& M, uint32_t na, uint32_t nb,
+                           const Workspace& ws, const PathOutPtrs& po, int block_threads,
+                           int grid_blocks, int sm_count, cudaStream_t st);
+
 // Inertial-washboard scan kernel over an item table of (point, first path);
 // gauss is 0 (no Gaussian noise) or the three-point law.
 cudaError_t launch_scan(bool pois, bool dich, int gauss, const PointConsts* pts_dev,

@@ -85,6 +85,14 @@ def lib():
         "sde_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
         "sde_scan": (ctypes.c_int, [_P, ctypes.POINTER(ScanPoint), ctypes.c_uint32,
                                     ctypes.POINTER(Stats), ctypes.c_double]),
+        "sde_scan_resume": (ctypes.c_int, [_P, ctypes.POINTER(Stats), ctypes.c_double]),
+        "sde_begin": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_uint64]),
+        "sde_advance": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(PathOut),
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+        "sde_checkpoint_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+        "sde_checkpoint": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
+        "sde_restore": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
         "sde_reduce_f64": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
         "sde_philox_words": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "sde_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
@@ -175,13 +183,8 @@ class Engine:
                                               ctypes.byref(s)))
         return b.value, s.value
 
-    def run(self, paths, dt, n_transient, n_avg, path_out=None):
-        """Enqueue a run; path_out: dict of torch CUDA tensors (X_f f64, v_f f32, vbar f64,
-        jP u32/i32, jD u32/i32), each of length `paths`."""
-        if path_out is None:
-            _check(self._ctx, lib().sde_run(self._ctx, int(paths), float(dt), int(n_transient),
-                                            int(n_avg)))
-            return
+    @staticmethod
+    def _path_out(path_out, paths):
         po = PathOut()
         for name, want in (("X_f", 8), ("v_f", 4), ("vbar", 8), ("jP", 4), ("jD", 4)):
             t = path_out.get(name)
@@ -191,8 +194,51 @@ class Engine:
                 raise ValueError("path_out[%s] must be a contiguous CUDA tensor of %d-byte elements "
                                  "and length >= paths" % (name, want))
             setattr(po, name, t.data_ptr())
+        return po
+
+    def run(self, paths, dt, n_transient, n_avg, path_out=None):
+        """Enqueue a run; path_out: dict of torch CUDA tensors (X_f f64, v_f f32, vbar f64,
+        jP u32/i32, jD u32/i32), each of length `paths`."""
+        if path_out is None:
+            _check(self._ctx, lib().sde_run(self._ctx, int(paths), float(dt), int(n_transient),
+                                            int(n_avg)))
+            return
+        po = self._path_out(path_out, paths)
         _check(self._ctx, lib().sde_run_paths(self._ctx, int(paths), float(dt), int(n_transient),
                                               int(n_avg), ctypes.byref(po)))
+
+    # segmented runs (sde_begin / sde_advance) and checkpoints
+
+    def begin(self, paths, dt, n_transient, n_avg):
+        """Start a segmented run with the current parameters and seed."""
+        self._seg_paths = int(paths)
+        _check(self._ctx, lib().sde_begin(self._ctx, int(paths), float(dt), int(n_transient),
+                                          int(n_avg)))
+
+    def advance(self, n_steps=0, path_out=None):
+        """Enqueue one segment of n_steps steps (0: to the end); returns the steps done.
+        path_out (as in run) is written by the segment that completes the run."""
+        done = ctypes.c_uint64()
+        po = None
+        if path_out is not None:
+            po = ctypes.byref(self._path_out(path_out, getattr(self, "_seg_paths", 0)))
+        _check(self._ctx, lib().sde_advance(self._ctx, int(n_steps), po, ctypes.byref(done)))
+        return done.value
+
+    def checkpoint(self) -> bytes:
+        """The segmented run's checkpoint (header and saved path states) as bytes."""
+        n = ctypes.c_uint64()
+        _check(self._ctx, lib().sde_checkpoint_size(self._ctx, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._ctx, lib().sde_checkpoint(self._ctx, buf, n.value))
+        return buf.raw
+
+    def restore(self, data: bytes):
+        """Continue the segmented run saved in `data` (from checkpoint())."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(self._ctx, lib().sde_restore(self._ctx, buf, len(data)))
+        import struct
+        self._seg_paths = struct.unpack_from("<Q", data, 168)[0]   # header field `paths`
 
     def stats(self) -> dict:
         s = Stats()
@@ -210,8 +256,16 @@ class Engine:
             arr[i].n_transient = int(pt["n_transient"])
             arr[i].n_avg = int(pt["n_avg"])
         out = (Stats * n)()
+        self._scan_n = n
         _check(self._ctx, lib().sde_scan(self._ctx, arr, n, out, float(deadline_ms)))
         return [o.as_dict() for o in out]
+
+    def scan_resume(self, deadline_ms=0.0):
+        """Finish the last scan after it raised SdeTimeout (items already done are kept)."""
+        n = getattr(self, "_scan_n", 0)
+        out = (Stats * max(n, 1))()
+        _check(self._ctx, lib().sde_scan_resume(self._ctx, out, float(deadline_ms)))
+        return [out[i].as_dict() for i in range(n)]
 
     def reduce_f64(self, vals):
         """vals: contiguous CUDA float64 tensor -> (n, sum, sum of squares)."""
