@@ -161,14 +161,14 @@ def run_engine(args):
     steps_per_path = n_tr + n_avg
     stream = torch.cuda.Stream()
     prm = E.make_params(**spec["params"])
-    shape = (128, 0)
+    from paper_1409_4923_gb300 import autotune
+    knobs = dict(autotune.DEFAULT)
     if not args.no_autotune:
-        from paper_1409_4923_gb300 import autotune
-        b, g, _ = autotune.tune(spec["model"], prm, dt, paths, n_probe_steps=2048,
-                                seed=spec["seed"] + rank, stream=stream)
-        shape = (b, g)
+        t = autotune.tune(spec["model"], prm, dt, paths, n_probe_steps=2048,
+                          seed=spec["seed"] + rank, stream=stream)
+        knobs = {f: t[f] for f in autotune.DEFAULT}
     eng = E.Engine(spec["model"], prm, seed=spec["seed"] + rank, stream=stream)
-    eng.set_tuning(*shape)
+    autotune.apply_tuning(eng, knobs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
 
     def one_step():
@@ -208,7 +208,7 @@ def run_engine(args):
         t0 = time.perf_counter()
         e = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
                      stream=stream)
-        e.set_tuning(*shape)
+        autotune.apply_tuning(e, knobs)
         e.run(paths, dt, n_tr, n_avg)
         e.stats()
         e.close()
@@ -238,7 +238,10 @@ def run_engine(args):
                    "parallelism": "paths sharded per GPU" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB device write) between timed steps",
                    "path_arith": "fp32", "accumulators": "fp64",
-                   "launch_shape": {"block_threads": shape[0], "grid_blocks": shape[1] or "persistent",
+                   "launch_shape": {"block_threads": knobs["block"],
+                                    "grid_blocks": knobs["grid"] or "persistent",
+                                    "paths_per_thread": knobs["ppt"],
+                                    "steps_per_launch": knobs["steps_per_launch"] or "whole run",
                                     "chosen_by": "fixed" if args.no_autotune else "autotuner"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops,
                      "unit": "Top/s (lane ops)", "frac": achieved / peak_tops,
@@ -333,7 +336,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="use the default launch shape instead of the autotuner's")
+                    help="use the default launch knobs instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -236,8 +236,26 @@ int sde_philox_words(sde_ctx* ctx, const uint32_t* ctr, uint64_t n, uint64_t see
  * autotuner of the Python layer picks it.  EINVAL outside those ranges. */
 int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
 
-/* Resident blocks per SM of this context's path kernel at `block_threads`,
- * and the device's SM count (host outputs). */
+/* Paths integrated by one GPU lane (1 or 2; default 1).  With 2, each lane
+ * advances two paths step by step, interleaved, so that their independent
+ * dependency chains hide each other's latencies and the drive values and
+ * loop work are shared; each path takes exactly the operations it takes with
+ * 1, so results do not change.  Applies to sde_run, sde_run_paths and the
+ * per-point launches of sde_scan for the overdamped models.  EINVAL otherwise. */
+int sde_set_paths_per_thread(sde_ctx* ctx, int paths_per_thread);
+
+/* Steps per kernel launch of sde_run / sde_run_paths (Algorithm 5's
+ * `samples`): 0 (default) runs the whole simulation in one launch; a
+ * multiple of 32 cuts it into launches of that many steps, with the path
+ * states kept in device memory between them (84 bytes per path, allocated on
+ * first use).  Cut points at multiples of 32 steps leave the results
+ * bit-identical.  For hosts whose kernels may not run longer than a watchdog
+ * limit.  EINVAL if not a multiple of 32. */
+int sde_set_steps_per_launch(sde_ctx* ctx, uint64_t steps);
+
+/* Resident blocks per SM of this context's path kernel at `block_threads`
+ * (and the context's paths per thread), and the device's SM count (host
+ * outputs). */
 int sde_occupancy(sde_ctx* ctx, int block_threads, int* blocks_per_sm, int* sm_count);
 
 /* Largest path count of sde_run_noalloc. */

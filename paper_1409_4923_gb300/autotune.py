@@ -1,12 +1,15 @@
-"""Launch-shape autotuner of the path kernels.
+"""Launch autotuner of the path kernels.
 
-The knobs are the threads per block (32 .. 128) and the grid (0 = one
-persistent wave sized by the occupancy calculator, or a fixed multiple of the
-SM count).  Results never depend on the shape (each 32-path warp item is
-integrated identically wherever it runs), so the tuner only times: it runs a
-short probe of the same kernel variant (same model and noise switches) for
-each candidate, keeps the fastest, and caches it per (device, variant, size
-class) in a JSON file.  Engine users apply it with `apply(engine, ...)`.
+Knobs: threads per block (32 .. 128), the grid (0 = one persistent wave sized
+by the occupancy calculator, or a fixed multiple of the SM count), paths per
+lane (1 or 2, interleaved) and steps per launch (0 = the whole run in one
+launch, or Algorithm 5's `samples` steps per launch with the path states kept
+in device memory between launches).  Results never depend on any of them (each
+path takes the same operations however it is scheduled; the tests check this
+bit for bit), so the tuner only times: it runs a short probe of the same
+kernel variant (same model and noise switches) for each candidate, keeps the
+fastest, and caches it per (device, variant, size class) in a JSON file.
+Engine users apply it with `apply(engine, ...)`.
 """
 import json
 import math
@@ -20,6 +23,9 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sde_gb300", "au
 
 BLOCKS = (32, 64, 96, 128)
 GRID_MULTIPLES = (0, 1, 2, 4)         # 0: persistent full-occupancy wave; k: k x SMs blocks
+PATHS_PER_THREAD = (1, 2)
+STEPS_PER_LAUNCH = (0, 1024)          # 0: whole run per launch
+DEFAULT = {"block": 128, "grid": 0, "ppt": 1, "steps_per_launch": 0}
 
 
 def cache_path():
@@ -52,16 +58,18 @@ def key(device_name, model, flags, paths):
 
 
 def candidates(sm_count):
+    """(block, grid, paths per thread) shapes; the default comes first."""
     out = []
-    for b in BLOCKS:
-        for g in GRID_MULTIPLES:
-            out.append((b, g * sm_count))
+    for ppt in PATHS_PER_THREAD:
+        for b in sorted(BLOCKS, reverse=True):
+            for g in GRID_MULTIPLES:
+                out.append((b, g * sm_count, ppt))
     return out
 
 
 def choose(timings):
-    """The fastest (block, grid) of {(block, grid): seconds}; ties go to the
-    earlier candidate (the default shape comes first)."""
+    """The fastest candidate of {candidate: seconds}; ties go to the earlier
+    candidate (the default comes first)."""
     best, best_t = None, float("inf")
     for cand, t in timings.items():
         if t < best_t * (1.0 - 1e-9):
@@ -69,45 +77,70 @@ def choose(timings):
     return best
 
 
+def _time_run(eng, paths, dt, steps):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng.run(paths, dt, 0, steps)
+    eng.stats()
+    return time.perf_counter() - t0
+
+
 def tune(model, params, dt, paths, n_probe_steps=2048, seed=0, stream=None, cache=None, force=False,
          log=None):
-    """Time every candidate shape on a probe of `paths` paths x n_probe_steps
-    steps (CUDA events) and cache the best; returns (block, grid, timings)."""
+    """Time every candidate on a probe of `paths` paths x n_probe_steps steps
+    (shape stage), then the steps-per-launch candidates on 2 x n_probe_steps
+    steps with the best shape; caches and returns a dict with keys block,
+    grid, ppt, steps_per_launch (and seconds, the probe timings, when it ran)."""
     import torch
     cache = cache or cache_path()
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
     k = key(dev, model, params.noise_flags, paths)
     data = _load(cache)
-    if not force and k in data:
-        b, g = data[k]["block"], data[k]["grid"]
-        return b, g, None
+    if not force and k in data and all(f in data[k] for f in DEFAULT):
+        return {f: data[k][f] for f in DEFAULT}
     eng = E.Engine(model, params, seed=seed, stream=stream)
     try:
         _, sms = eng.occupancy(128)
-        timings = {}
         eng.run(paths, dt, 0, n_probe_steps)         # warm-up (module load, workspace)
         eng.stats()
-        for b, g in candidates(sms):
+        shapes = {}
+        for b, g, ppt in candidates(sms):
+            eng.set_paths_per_thread(ppt)
             eng.set_tuning(b, g)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            eng.run(paths, dt, 0, n_probe_steps)
-            eng.stats()
-            timings[(b, g)] = time.perf_counter() - t0
+            shapes[(b, g, ppt)] = _time_run(eng, paths, dt, n_probe_steps)
             if log:
-                log("block %3d grid %5d: %.3f ms" % (b, g, timings[(b, g)] * 1e3))
-        b, g = choose(timings)
+                log("block %3d grid %5d ppt %d: %.3f ms" % (b, g, ppt, shapes[(b, g, ppt)] * 1e3))
+        b, g, ppt = choose(shapes)
+        eng.set_paths_per_thread(ppt)
+        eng.set_tuning(b, g)
+        spl = {}
+        for s in STEPS_PER_LAUNCH:
+            eng.set_steps_per_launch(s)
+            _time_run(eng, paths, dt, 2 * n_probe_steps)          # allocates the saved states once
+            spl[s] = _time_run(eng, paths, dt, 2 * n_probe_steps)
+            if log:
+                log("steps per launch %d: %.3f ms" % (s, spl[s] * 1e3))
+        s = choose(spl)
     finally:
         eng.close()
+    res = {"block": b, "grid": g, "ppt": ppt, "steps_per_launch": s}
     data = _load(cache)
-    data[k] = {"block": b, "grid": g, "probe_paths": paths, "probe_steps": n_probe_steps,
-               "seconds": {"%d,%d" % bg: t for bg, t in timings.items()}}
+    data[k] = dict(res, probe_paths=paths, probe_steps=n_probe_steps,
+                   seconds={"%d,%d,%d" % c: t for c, t in shapes.items()},
+                   seconds_steps_per_launch={str(c): t for c, t in spl.items()})
     _store(cache, data)
-    return b, g, timings
+    return dict(res, seconds=shapes, seconds_steps_per_launch=spl)
+
+
+def apply_tuning(engine, t):
+    engine.set_tuning(t["block"], t["grid"])
+    engine.set_paths_per_thread(t["ppt"])
+    engine.set_steps_per_launch(t["steps_per_launch"])
 
 
 def apply(engine, model, params, dt, paths, **kw):
-    """Tune (or read the cache) and set the engine's launch shape."""
-    b, g, _ = tune(model, params, dt, paths, **kw)
-    engine.set_tuning(b, g)
-    return b, g
+    """Tune (or read the cache) and set the engine's launch knobs."""
+    t = tune(model, params, dt, paths, **kw)
+    apply_tuning(engine, t)
+    return t

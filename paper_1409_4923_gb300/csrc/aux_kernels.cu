@@ -4,32 +4,32 @@
 
 namespace sde {
 
-cudaError_t launch_point_m0(bool, bool, int, const PointConsts&, const LaunchConsts&,
-                            const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t);
-cudaError_t launch_point_m1(bool, bool, int, const PointConsts&, const LaunchConsts&,
-                            const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t);
-cudaError_t launch_point_m2(bool, bool, int, const PointConsts&, const LaunchConsts&,
-                            const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t);
+#define SDE_POINT_DECL(M, PPT) \
+cudaError_t launch_point_m##M##_p##PPT(bool, bool, int, const PointConsts&, const LaunchConsts&, \
+                                      const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t); \
+int blocks_per_sm_m##M##_p##PPT(bool, bool, int, int);
+SDE_POINT_DECL(0, 1) SDE_POINT_DECL(1, 1) SDE_POINT_DECL(2, 1)
+SDE_POINT_DECL(0, 2) SDE_POINT_DECL(1, 2) SDE_POINT_DECL(2, 2)
+#undef SDE_POINT_DECL
 #define SDE_SEG_DECL(M) \
 cudaError_t launch_segment_m##M(bool, bool, int, const PointConsts&, const LaunchConsts&, \
                                 const StatePlanes&, uint32_t, uint32_t, const Workspace&, \
                                 const PathOutPtrs&, int, int, int, cudaStream_t);
 SDE_SEG_DECL(0) SDE_SEG_DECL(1) SDE_SEG_DECL(2)
 #undef SDE_SEG_DECL
-int blocks_per_sm_m0(bool, bool, int, int);
-int blocks_per_sm_m1(bool, bool, int, int);
-int blocks_per_sm_m2(bool, bool, int, int);
 
-cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+cudaError_t launch_point(int model, bool pois, bool dich, int gauss, int ppt, const PointConsts& P,
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                          int bt, int gb, int sm, cudaStream_t st)
 {
+#define SDE_M(M) \
+    case M: return ppt == 2 ? launch_point_m##M##_p2(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st) \
+                            : launch_point_m##M##_p1(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
     switch (model) {
-    case kModelInertial: return launch_point_m0(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
-    case kModelOverdampedWashboard: return launch_point_m1(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
-    case kModelPWL: return launch_point_m2(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
+    SDE_M(0) SDE_M(1) SDE_M(2)
     default: return cudaErrorInvalidValue;
     }
+#undef SDE_M
 }
 
 cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const PointConsts& P,
@@ -46,14 +46,16 @@ cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const Poi
     }
 }
 
-int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int bt)
+int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int ppt, int bt)
 {
+#define SDE_M(M) \
+    case M: return ppt == 2 ? blocks_per_sm_m##M##_p2(pois, dich, gauss, bt) \
+                            : blocks_per_sm_m##M##_p1(pois, dich, gauss, bt);
     switch (model) {
-    case kModelInertial: return blocks_per_sm_m0(pois, dich, gauss, bt);
-    case kModelOverdampedWashboard: return blocks_per_sm_m1(pois, dich, gauss, bt);
-    case kModelPWL: return blocks_per_sm_m2(pois, dich, gauss, bt);
+    SDE_M(0) SDE_M(1) SDE_M(2)
     default: return 0;
     }
+#undef SDE_M
 }
 
 // ---------------------------------------------------------------- batched scan
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(256) reduce_items_kernel(const double* __restr
     const double v = valid ? vals[i] : 0.0;
     const double a = warp_sum(valid ? 1.0 : 0.0);
     const double b = warp_sum(v);
-    const double c = warp_sum(v * v);
+    const double c = warp_sum(__dmul_rn(v, v));
     if (lane == 0u && gw * 32ull < n) {
         double* o = partials + 5ull * gw;
         o[0] = a; o[1] = b; o[2] = c; o[3] = 0.0; o[4] = 0.0;

@@ -106,6 +106,10 @@ struct sde_ctx {
     // tuning
     int block_threads = 128;
     int grid_blocks = 0;          // 0 = persistent grid from occupancy
+    int paths_per_thread = 1;     // paths integrated by one lane, interleaved
+    uint64_t steps_per_launch = 0;   // 0 = a whole run per launch
+    void* run_state = nullptr;    // saved states of runs cut into launches
+    size_t run_state_bytes = 0;
     // scan graphs keyed by (npts, n_items, flags, budget)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, ScanGraph> graphs;
     // bumped by every call that writes the workspace; a timed-out scan can be
@@ -399,12 +403,32 @@ int sde_set_tuning(sde_ctx* c, int block_threads, int grid_blocks)
     return SDE_OK;
 }
 
+int sde_set_paths_per_thread(sde_ctx* c, int paths_per_thread)
+{
+    if (!c) return SDE_EINVAL;
+    if (paths_per_thread != 1 && paths_per_thread != 2)
+        return fail(c, SDE_EINVAL, "paths_per_thread must be 1 or 2");
+    if (paths_per_thread != c->paths_per_thread) drop_graphs(c);
+    c->paths_per_thread = paths_per_thread;
+    return SDE_OK;
+}
+
+int sde_set_steps_per_launch(sde_ctx* c, uint64_t steps)
+{
+    if (!c) return SDE_EINVAL;
+    if (steps % 32u != 0u || steps > kMaxSteps)
+        return fail(c, SDE_EINVAL, "steps_per_launch must be a multiple of 32 (0 = whole run)");
+    c->steps_per_launch = steps;
+    return SDE_OK;
+}
+
 int sde_occupancy(sde_ctx* c, int block_threads, int* blocks_per_sm, int* sm_count)
 {
     if (!c || !blocks_per_sm || !sm_count) return SDE_EINVAL;
     const uint32_t f = c->p.noise_flags;
     *blocks_per_sm = point_blocks_per_sm((int)c->model, (f & SDE_NOISE_POISSON) != 0,
-                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p), block_threads);
+                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p),
+                                         c->paths_per_thread, block_threads);
     *sm_count = c->sm_count;
     return SDE_OK;
 }
@@ -434,9 +458,36 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
     if (out) po = PathOutPtrs{out->X_f, out->v_f, out->vbar, out->jP, out->jD};
     const LaunchConsts K = make_launch(c->seed, (uint32_t)items, 0);
     const uint32_t f = c->p.noise_flags;
-    SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
-                             gauss_kind(c->p), P, K, ws, po, c->block_threads, c->grid_blocks,
-                             c->sm_count, c->stream));
+    const uint64_t total = n_tr + n_avg;
+    if (c->steps_per_launch == 0 || c->steps_per_launch >= total) {
+        SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+                                 gauss_kind(c->p), c->paths_per_thread, P, K, ws, po, c->block_threads,
+                                 c->grid_blocks, c->sm_count, c->stream));
+    } else {
+        // Algorithm 5 with `samples` = steps_per_launch: the path states stay
+        // in device memory between launches; cut points are multiples of 32
+        // steps, so the results are those of one launch bit for bit
+        const size_t need = (size_t)kStateBytesPerPath * items * 32ull;
+        if (need > c->run_state_bytes) {
+            if (c->run_state) {
+                cudaStreamSynchronize(c->stream);
+                cudaFree(c->run_state);
+                c->run_state = nullptr;
+                c->run_state_bytes = 0;
+            }
+            SDE_CUDA(c, cudaMalloc(&c->run_state, need));
+            c->run_state_bytes = need;
+        }
+        const StatePlanes M{(unsigned char*)c->run_state, (uint32_t)(items * 32ull)};
+        for (uint64_t na = 0; na < total; na += c->steps_per_launch) {
+            const uint64_t nb = std::min(total, na + c->steps_per_launch);
+            if (na > 0) SDE_CUDA(c, cudaMemsetAsync(base, 0, 4, c->stream));
+            SDE_CUDA(c, launch_segment((int)c->model, (f & SDE_NOISE_POISSON) != 0,
+                                       (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p), P, K, M,
+                                       (uint32_t)na, (uint32_t)nb, ws, po, c->block_threads,
+                                       c->grid_blocks, c->sm_count, c->stream));
+        }
+    }
     SDE_CUDA(c, launch_fold(ws.partials, ranges, 1, out5, c->stream));
     SDE_CUDA(c, cudaMemcpyAsync(c->host, out5, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SDE_CUDA(c, cudaMemcpyAsync(c->host + 5, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -571,7 +622,8 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * ranges[i].x};
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (flags & SDE_NOISE_POISSON) != 0,
-                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(pts[i].p), P[i], K, wsi,
+                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(pts[i].p),
+                                     c->paths_per_thread, P[i], K, wsi,
                                      po, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
         SDE_CUDA(c, launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream));
@@ -638,7 +690,8 @@ int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)
             Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * S.ranges[i].x};
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (S.flags & SDE_NOISE_POISSON) != 0,
-                                     (S.flags & SDE_NOISE_DICHOT) != 0, S.gauss[i], S.P[i], K, wsi, po,
+                                     (S.flags & SDE_NOISE_DICHOT) != 0, S.gauss[i], c->paths_per_thread,
+                                     S.P[i], K, wsi, po,
                                      c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
     }
@@ -898,6 +951,7 @@ void sde_destroy(sde_ctx* c)
     drop_graphs(c);
     if (c->ws) cudaFree(c->ws);
     if (c->state) cudaFree(c->state);
+    if (c->run_state) cudaFree(c->run_state);
     if (c->host) cudaFreeHost(c->host);
     if (c->done) cudaEventDestroy(c->done);
     if (c->own_stream) cudaStreamDestroy(c->stream);

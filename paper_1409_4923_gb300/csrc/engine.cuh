@@ -125,7 +125,7 @@ __device__ __forceinline__ int32_t wait_steps(uint32_t w, float cl2, double inv_
     y = fminf(y, 1.0e9f);
     const float fl = floorf(y);
     const float fr = y - fl;
-    const float m = (cl2 + y) * 0x1p-16f;
+    const float m = __fmul_rn(cl2 + y, 0x1p-16f);
     if (fr < m || fr > 1.0f - m) {
         const double q = -inv_rate * log((double)u) / dt;
         return (int32_t)fmin(floor(q), 1.0e9);
@@ -180,16 +180,20 @@ __device__ __forceinline__ void fold(PathState& S)
 // the overdamped coordinates are folded every step.
 template <int MODEL> struct FoldPerStep { static constexpr bool value = MODEL != kModelInertial; };
 
-// -V'(coordinate) x dt in coordinate units.
+// base + (-V'(coordinate) x dt) in coordinate units.  Every multiply-add of
+// the path is written out (fmaf, or a rounded product __fmul_rn / __dmul_rn
+// where no fusion is wanted), so that the compiler's contraction choices
+// cannot differ between the kernels that share this code (one or two paths
+// per lane, segments, scans) and their results stay bit-identical.
 template <int MODEL>
-__device__ __forceinline__ float force_dt(float c, const PointConsts& P)
+__device__ __forceinline__ float add_force_dt(float base, float c, const PointConsts& P)
 {
     if (MODEL == kModelPWL) {
         // V' = +1 on [-1, 0), -1 on [0, 1) (mod 2): force -V0 V'
-        const float y = c - 2.0f * floorf((c + 1.0f) * 0.5f);
-        return y < 0.0f ? -P.fdt : P.fdt;
+        const float y = fmaf(-2.0f, floorf(__fmul_rn(c + 1.0f, 0.5f)), c);
+        return base + (y < 0.0f ? -P.fdt : P.fdt);
     } else {
-        return -P.fdt * cos_sfu(c);
+        return fmaf(-P.fdt, cos_sfu(c), base);
     }
 }
 
@@ -209,27 +213,27 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
                                         float jump, float d0, float d1)
 {
     if (MODEL == kModelInertial) {
-        const float b1 = fmaf(-P.gdt, S.v, d0) + force_dt<MODEL>(S.c, P);   // F1_v dt
+        const float b1 = add_force_dt<MODEL>(fmaf(-P.gdt, S.v, d0), S.c, P);   // F1_v dt
         const float vxi = S.v + dxi;
         float cb = fmaf(P.wdt, S.v, S.c);                                   // Euler x
         float vb = vxi + b1;                                                // Euler v
-        const float b2 = fmaf(-P.gdt, vb, d1) + force_dt<MODEL>(cb, P);
+        const float b2 = add_force_dt<MODEL>(fmaf(-P.gdt, vb, d1), cb, P);
         const float ch = fmaf(P.whdt, S.v, S.c);
         const float h1 = fmaf(0.5f, b1, vxi);
         cb = fmaf(P.whdt, vb, ch);                                          // predictor x
         vb = fmaf(0.5f, b2, h1);                                            // predictor v
-        const float b3 = fmaf(-P.gdt, vb, d1) + force_dt<MODEL>(cb, P);
+        const float b3 = add_force_dt<MODEL>(fmaf(-P.gdt, vb, d1), cb, P);
         S.c = fmaf(P.whdt, vb, ch);                                         // corrector x
         S.v = fmaf(0.5f, b3, h1 + jump);                                    // corrector v
         accumulate<ACC>(S);
     } else {
-        const float b1 = d0 + force_dt<MODEL>(S.c, P);
+        const float b1 = add_force_dt<MODEL>(d0, S.c, P);
         const float cxi = S.c + dxi;
         float cb = cxi + b1;                                                // Euler
-        const float b2 = d1 + force_dt<MODEL>(cb, P);
+        const float b2 = add_force_dt<MODEL>(d1, cb, P);
         const float h1 = fmaf(0.5f, b1, cxi);
         cb = fmaf(0.5f, b2, h1);                                            // predictor
-        const float b3 = d1 + force_dt<MODEL>(cb, P);
+        const float b3 = add_force_dt<MODEL>(d1, cb, P);
         S.c = fmaf(0.5f, b3, h1 + jump);                                    // corrector
     }
     if (FOLD) fold<MODEL>(S);
@@ -351,12 +355,12 @@ __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const Poi
     if (GAUSS == kGaussNormal) {
         const uint32_t wa = k < 2u ? w.x : w.z;
         const uint32_t wb = k < 2u ? w.y : w.w;
-        const float R = sqrtf(-2.0f * __logf(u24(wa)));
+        const float R = sqrtf(__fmul_rn(-2.0f, __logf(u24(wa))));
         // angle 2 pi phi - pi in [-pi, pi): cos/sin change sign
         const float T = fmaf(6.2831853071795865f, phi24(wb), -3.14159265358979f);
         float s, c;
         __sincosf(T, &s, &c);
-        return -P.xi_c * R * ((k & 1u) ? s : c);
+        return __fmul_rn(__fmul_rn(-P.xi_c, R), (k & 1u) ? s : c);
     } else {
         return 0.0f;
     }
@@ -525,10 +529,10 @@ struct PathResult {
 template <int MODEL, bool POIS, bool DICH>
 __device__ __forceinline__ void finish_path(const PathState& S, const PointConsts& P, PathResult& R)
 {
-    const double dX = ((double)S.kf - (double)S.kf_i) * P.period
-                    + ((double)S.c - (double)S.c_i) * P.coord_to_x;
-    R.X_f = (double)S.kf * P.period + (double)S.c * P.coord_to_x;
-    R.vbar = dX * P.inv_window;
+    const double dX = __fma_rn((double)S.kf - (double)S.kf_i, P.period,
+                               __dmul_rn((double)S.c - (double)S.c_i, P.coord_to_x));
+    R.X_f = __fma_rn((double)S.kf, P.period, __dmul_rn((double)S.c, P.coord_to_x));
+    R.vbar = __dmul_rn(dX, P.inv_window);
     R.sum_v = S.svd + (double)S.sv;
     R.sum_v2 = S.sv2d + (double)S.sv2;
     R.v_f = S.v;
@@ -569,6 +573,189 @@ __device__ __forceinline__ void advance_path(PathState& S, const PointConsts& P,
     if (nb > ntr)
         run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane,
                                                                      max(na, ntr), nb);
+}
+
+// ---------------------------------------------------------------- several paths per lane
+
+// The same integration for PPT paths per lane, interleaved step by step so
+// that their independent dependency chains fill each other's latencies; the
+// drive values and the loop are shared.  Every path takes exactly the
+// operations of run_steps (a chunk whose Poisson events do not fit the queue
+// of some path takes all paths' events inline, which gives the same values),
+// so results do not depend on PPT.
+
+template <bool POIS, bool DICH, int PPT>
+__device__ __forceinline__ bool chunk_events_multi(PathState (&S)[PPT], const PointConsts& P,
+                                                   const LaunchConsts& K, const uint32_t (&path)[PPT],
+                                                   uint32_t n0, uint32_t (&pm)[PPT], float (&z0)[PPT],
+                                                   float (&z1)[PPT], float (&z2)[PPT], uint32_t (&dm)[PPT])
+{
+    bool over = false;
+    uint32_t e_save[PPT], J_save[PPT], w2_save[PPT], w3_save[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        pm[p] = 0u;
+        z0[p] = z1[p] = z2[p] = 0.0f;
+        dm[p] = 0u;
+        if (POIS) {
+            e_save[p] = S[p].eP; J_save[p] = S[p].JP; w2_save[p] = S[p].pw2; w3_save[p] = S[p].pw3;
+            uint32_t cnt = 0u;
+            while (S[p].eP < n0 + 32u && cnt < 4u) {
+                const uint32_t off = S[p].eP - n0;
+                const float z = pois_event(S[p], P, K, path[p]);
+                pm[p] |= 1u << off;
+                z0[p] = cnt == 0u ? z : z0[p];
+                z1[p] = cnt == 1u ? z : z1[p];
+                z2[p] = cnt == 2u ? z : z2[p];
+                ++cnt;
+            }
+            over |= cnt > 3u;
+        }
+        if (DICH) {
+            dm[p] = S[p].dst ? 0xffffffffu : 0u;
+            while (S[p].eD < n0 + 32u) {
+                const uint32_t off = S[p].eD - n0;
+                dich_event(S[p], P, K, path[p]);
+                dm[p] ^= 0xffffffffu << off;
+            }
+        }
+    }
+    if (POIS && __any_sync(0xffffffffu, over)) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            S[p].eP = e_save[p]; S[p].JP = J_save[p]; S[p].pw2 = w2_save[p]; S[p].pw3 = w3_save[p];
+        }
+        return false;
+    }
+    return true;
+}
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST, int PPT>
+__device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const PointConsts& P,
+                                                  const LaunchConsts& K, const uint32_t (&path)[PPT],
+                                                  uint32_t n0, float dch, float& dcur, uint4 (&w)[PPT],
+                                                  uint32_t (&pm)[PPT], float (&z0)[PPT], float (&z1)[PPT],
+                                                  float (&z2)[PPT], uint32_t (&dm)[PPT])
+{
+    uint4 wn[PPT];
+#pragma unroll 1
+    for (uint32_t g = 0; g < 8u; ++g) {
+        uint32_t r[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            r[p] = 0u;
+            if (GAUSS == kGauss3Point) {
+                if ((g & 3u) == 0u) wn[p] = stream(K, P.c1_gauss, path[p], (n0 >> 4) + (g >> 2) + 1u);
+                const uint32_t q = g & 3u;
+                r[p] = q == 0u ? w[p].x : (q == 1u ? w[p].y : (q == 2u ? w[p].z : w[p].w));
+            } else if (GAUSS == kGaussNormal) {
+                wn[p] = stream(K, P.c1_gauss, path[p], (n0 >> 2) + g + 1u);
+            }
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) {
+            const float dnext = __shfl_sync(0xffffffffu, dch, (int)(g * 4u + k));
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                float dxi = 0.0f;
+                if (GAUSS == kGauss3Point) dxi = three_point(r[p], P);
+                else if (GAUSS == kGaussNormal) dxi = gauss_inc<GAUSS>(w[p], k, P);
+                float jump = 0.0f;
+                if (POIS) {
+                    if (FAST) {
+                        const bool kick = (pm[p] & (1u << k)) != 0u;
+                        jump = kick ? z0[p] : -P.aP_dt;
+                        z0[p] = kick ? z1[p] : z0[p];
+                        z1[p] = kick ? z2[p] : z1[p];
+                    } else {
+                        jump = -P.aP_dt;
+                        if (n0 + g * 4u + k == S[p].eP) jump = pois_event(S[p], P, K, path[p]);
+                    }
+                }
+                if (DICH) jump += (dm[p] & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
+                pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S[p], P, dxi, jump, dcur, dnext);
+            }
+            dcur = dnext;
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (GAUSS == kGaussNormal || (GAUSS == kGauss3Point && (g & 3u) == 3u)) w[p] = wn[p];
+            pm[p] >>= 4;
+            dm[p] >>= 4;
+            if (!FoldPerStep<MODEL>::value) fold<MODEL>(S[p]);
+        }
+    }
+}
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, int PPT>
+__device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const PointConsts& P,
+                                                const LaunchConsts& K, const uint32_t (&path)[PPT],
+                                                uint32_t lane, uint32_t n, uint32_t n_end)
+{
+    uint32_t head = n;
+    if ((n & 31u) != 0u) head = min(n_end, (n + 31u) & ~31u);
+    if (head > n) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p)
+            single_steps<MODEL, POIS, DICH, GAUSS, ACC>(S[p], P, K, path[p], n, head);
+        n = head;
+    }
+    if (n + 32u <= n_end) {
+        float dcur = drive_at(n, P);
+        uint4 w[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            w[p] = make_uint4(0u, 0u, 0u, 0u);
+            if (GAUSS == kGauss3Point) w[p] = stream(K, P.c1_gauss, path[p], n >> 4);
+            else if (GAUSS == kGaussNormal) w[p] = stream(K, P.c1_gauss, path[p], n >> 2);
+        }
+        for (; n + 32u <= n_end; n += 32u) {
+            const float dch = drive_at(n + 1u + lane, P);
+            uint32_t pm[PPT], dm[PPT];
+            float z0[PPT], z1[PPT], z2[PPT];
+            if (chunk_events_multi<POIS, DICH, PPT>(S, P, K, path, n, pm, z0, z1, z2, dm))
+                chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, true, PPT>(S, P, K, path, n, dch, dcur, w,
+                                                                            pm, z0, z1, z2, dm);
+            else
+                chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, false, PPT>(S, P, K, path, n, dch, dcur,
+                                                                             w, pm, z0, z1, z2, dm);
+            if (ACC && ((n + 32u) & 255u) == 0u) {
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    S[p].svd += (double)S[p].sv;
+                    S[p].sv2d += (double)S[p].sv2;
+                    S[p].sv = 0.0f;
+                    S[p].sv2 = 0.0f;
+                }
+            }
+        }
+    }
+    if (n < n_end) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p)
+            single_steps<MODEL, POIS, DICH, GAUSS, ACC>(S[p], P, K, path[p], n, n_end);
+    }
+}
+
+template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
+__device__ __forceinline__ void simulate_paths(const PointConsts& P, const LaunchConsts& K,
+                                               const uint32_t (&path)[PPT], uint32_t lane,
+                                               PathResult (&R)[PPT])
+{
+    PathState S[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) init_path<MODEL, POIS, DICH>(S[p], P, K, path[p]);
+    run_steps_multi<MODEL, POIS, DICH, GAUSS, false, PPT>(S, P, K, path, lane, 0u, P.n_tr);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if (!FoldPerStep<MODEL>::value) fold<MODEL>(S[p]);
+        S[p].c_i = S[p].c;
+        S[p].kf_i = S[p].kf;
+    }
+    run_steps_multi<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial, PPT>(S, P, K, path, lane, P.n_tr,
+                                                                            P.n_tr + P.n_avg);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) finish_path<MODEL, POIS, DICH>(S[p], P, R[p]);
 }
 
 // ---------------------------------------------------------------- saved state
@@ -631,11 +818,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Pull the next warp item (lane 0 increments the counter); UINT32_MAX = done.
+// Pull the next warp item, or the first of `count` consecutive items (lane 0
+// increments the counter); UINT32_MAX = done.
 // With a budget, a warp that has run longer than it since t0 takes no further
 // item and marks the launch as timed out (the host reads the status word).
 __device__ __forceinline__ uint32_t next_item(uint32_t* counter, int32_t* status,
-                                              const LaunchConsts& K, uint32_t lane, uint64_t t0)
+                                              const LaunchConsts& K, uint32_t lane, uint64_t t0,
+                                              uint32_t count = 1u)
 {
     uint32_t item = 0u;
     if (lane == 0u) {
@@ -643,7 +832,7 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* counter, int32_t* status
             atomicExch(status, kStatusTimedOut);
             item = 0xffffffffu;
         } else {
-            item = atomicAdd(counter, 1u);
+            item = atomicAdd(counter, count);
         }
     }
     item = __shfl_sync(0xffffffffu, item, 0);
@@ -656,7 +845,7 @@ __device__ __forceinline__ void store_partial(double* partials, uint32_t item, u
 {
     const double n = warp_sum(valid ? 1.0 : 0.0);
     const double s1 = warp_sum(valid ? R.vbar : 0.0);
-    const double s2 = warp_sum(valid ? R.vbar * R.vbar : 0.0);
+    const double s2 = warp_sum(valid ? __dmul_rn(R.vbar, R.vbar) : 0.0);
     const double s3 = warp_sum(valid ? R.sum_v : 0.0);
     const double s4 = warp_sum(valid ? R.sum_v2 : 0.0);
     if (lane == 0u) {

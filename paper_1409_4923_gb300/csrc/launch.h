@@ -13,9 +13,10 @@ struct Workspace {
     double* partials;    // 5 doubles per warp item
 };
 
-// Launch the single-point path kernel for (model, poisson, dichotomous, gauss).
-// grid_blocks == 0 picks a persistent grid from the occupancy calculator.
-cudaError_t launch_point(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+// Launch the single-point path kernel for (model, poisson, dichotomous, gauss)
+// with ppt (1 or 2) paths per lane.  grid_blocks == 0 picks a persistent grid
+// from the occupancy calculator.
+cudaError_t launch_point(int model, bool pois, bool dich, int gauss, int ppt, const PointConsts& P,
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                          int block_threads, int grid_blocks, int sm_count, cudaStream_t st);
 
@@ -46,6 +47,6 @@ cudaError_t launch_philox(const uint4* ctr, uint64_t n, const LaunchConsts& K, u
                           cudaStream_t st);
 
 // Occupancy-derived resident blocks per SM for the kernel a launch would use.
-int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int block_threads);
+int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int ppt, int block_threads);
 
 }  // namespace sde

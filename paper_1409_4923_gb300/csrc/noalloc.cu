@@ -93,7 +93,7 @@ extern "C" int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t se
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_point((int)model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
-                         gauss_kind(*p), P, K, ws, po, 128, 0, sm_count, st);
+                         gauss_kind(*p), 1, P, K, ws, po, 128, 0, sm_count, st);
     if (e == cudaSuccess) e = launch_fold(ws.partials, range, 1, out5, st);
     if (e == cudaSuccess && status_out) {
         noalloc_end<<<1, 1, 0, st>>>(ws.status, status_out);

@@ -1,18 +1,9 @@
-// point_inertial.cu -- instantiations of the single-point path kernel for model 0.
+// point_inertial.cu -- instantiations of the single-point path kernel for model 0 (inertial washboard),
+// 1 path per lane.
 #include "point_kernels.cuh"
 
 namespace sde {
 
-cudaError_t launch_point_m0(bool pois, bool dich, int gauss, const PointConsts& P,
-                              const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
-                              int bt, int gb, int sm, cudaStream_t st)
-{
-    return launch_point_model<0>(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st);
-}
-
-int blocks_per_sm_m0(bool pois, bool dich, int gauss, int bt)
-{
-    return blocks_per_sm_model<0>(pois, dich, gauss, bt);
-}
+SDE_POINT_UNIT(0, 1)
 
 }  // namespace sde

@@ -5,9 +5,10 @@
 namespace sde {
 
 // Persistent warp-item kernel for one parameter point: each warp pulls
-// 32-path items, integrates its lane's path for n_transient + n_avg steps
-// and writes the item's FP64 partial sums (and, optionally, per-path results).
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+// 32-path items (PPT consecutive items at a time, one path of each per lane),
+// integrates its lanes' paths for n_transient + n_avg steps and writes each
+// item's FP64 partial sums (and, optionally, per-path results).
+template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
 __global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ PointConsts P,
                                                     const __grid_constant__ LaunchConsts K,
                                                     uint32_t* __restrict__ counter,
@@ -18,29 +19,44 @@ __global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ Poin
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t t0 = K.budget_ns ? globaltimer_ns() : 0ull;
     for (;;) {
-        const uint32_t item = next_item(counter, status, K, lane, t0);
+        const uint32_t item = next_item(counter, status, K, lane, t0, (uint32_t)PPT);
         if (item == 0xffffffffu) break;
-        const uint32_t path = item * 32u + lane;
-        const bool valid = path < P.n_paths;
-        PathResult R;
-        simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, path, lane, R);
-        if (valid) store_path(po, path, R);
-        store_partial(partials, item, lane, valid, R);
+        if (PPT == 1) {
+            const uint32_t path = item * 32u + lane;
+            const bool valid = path < P.n_paths;
+            PathResult R;
+            simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, path, lane, R);
+            if (valid) store_path(po, path, R);
+            store_partial(partials, item, lane, valid, R);
+        } else {
+            uint32_t path[PPT];
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) path[p] = (item + (uint32_t)p) * 32u + lane;
+            PathResult R[PPT];
+            simulate_paths<MODEL, POIS, DICH, GAUSS, PPT>(P, K, path, lane, R);
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                if (item + (uint32_t)p >= K.n_items) break;      // past the last item: no output
+                const bool valid = path[p] < P.n_paths;
+                if (valid) store_path(po, path[p], R[p]);
+                store_partial(partials, item + (uint32_t)p, lane, valid, R[p]);
+            }
+        }
     }
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
 cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Workspace& ws,
                            const PathOutPtrs& po, int block_threads, int grid_blocks,
                            int sm_count, cudaStream_t st)
 {
-    auto kern = point_kernel<MODEL, POIS, DICH, GAUSS>;
+    auto kern = point_kernel<MODEL, POIS, DICH, GAUSS, PPT>;
     if (grid_blocks <= 0) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_threads, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
-        const uint64_t warps = (uint64_t)K.n_items;
+        const uint64_t warps = ((uint64_t)K.n_items + PPT - 1) / PPT;
         const uint64_t need = (warps * 32ull + block_threads - 1) / block_threads;
         uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count;
         grid_blocks = (int)(need < cap ? need : cap);
@@ -50,25 +66,25 @@ cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Wo
     return cudaGetLastError();
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
 int blocks_per_sm_t(int block_threads)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, point_kernel<MODEL, POIS, DICH, GAUSS>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, point_kernel<MODEL, POIS, DICH, GAUSS, PPT>,
                                                   block_threads, 0);
     return per_sm;
 }
 
-// Dispatch over the noise switches for one model (instantiated per model in
-// its own translation unit).
-template <int MODEL>
+// Dispatch over the noise switches for one model and paths-per-lane count
+// (each pair instantiated in its own translation unit).
+template <int MODEL, int PPT>
 cudaError_t launch_point_model(bool pois, bool dich, int gauss, const PointConsts& P,
                                const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                                int bt, int gb, int sm, cudaStream_t st)
 {
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) \
-        return launch_point_t<MODEL, PO, DI, GA>(P, K, ws, po, bt, gb, sm, st);
+        return launch_point_t<MODEL, PO, DI, GA, PPT>(P, K, ws, po, bt, gb, sm, st);
     SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
     SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
     SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
@@ -79,11 +95,11 @@ cudaError_t launch_point_model(bool pois, bool dich, int gauss, const PointConst
     return cudaErrorInvalidValue;
 }
 
-template <int MODEL>
+template <int MODEL, int PPT>
 int blocks_per_sm_model(bool pois, bool dich, int gauss, int bt)
 {
 #define SDE_CASE(PO, DI, GA) \
-    if (pois == PO && dich == DI && gauss == GA) return blocks_per_sm_t<MODEL, PO, DI, GA>(bt);
+    if (pois == PO && dich == DI && gauss == GA) return blocks_per_sm_t<MODEL, PO, DI, GA, PPT>(bt);
     SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
     SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
     SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
@@ -93,5 +109,18 @@ int blocks_per_sm_model(bool pois, bool dich, int gauss, int bt)
 #undef SDE_CASE
     return 0;
 }
+
+// Instantiation unit of one (model, paths per lane) pair.
+#define SDE_POINT_UNIT(M, PPT) \
+    cudaError_t launch_point_m##M##_p##PPT(bool pois, bool dich, int gauss, const PointConsts& P, \
+                                          const LaunchConsts& K, const Workspace& ws, \
+                                          const PathOutPtrs& po, int bt, int gb, int sm, cudaStream_t st) \
+    { \
+        return launch_point_model<M, PPT>(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st); \
+    } \
+    int blocks_per_sm_m##M##_p##PPT(bool pois, bool dich, int gauss, int bt) \
+    { \
+        return blocks_per_sm_model<M, PPT>(pois, dich, gauss, bt); \
+    }
 
 }  // namespace sde

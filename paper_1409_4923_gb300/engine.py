@@ -96,6 +96,8 @@ def lib():
         "sde_reduce_f64": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
         "sde_philox_words": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "sde_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "sde_set_paths_per_thread": (ctypes.c_int, [_P, ctypes.c_int]),
+        "sde_set_steps_per_launch": (ctypes.c_int, [_P, ctypes.c_uint64]),
         "sde_occupancy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
         "sde_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
@@ -176,6 +178,12 @@ class Engine:
 
     def set_tuning(self, block_threads=128, grid_blocks=0):
         _check(self._ctx, lib().sde_set_tuning(self._ctx, int(block_threads), int(grid_blocks)))
+
+    def set_paths_per_thread(self, ppt=1):
+        _check(self._ctx, lib().sde_set_paths_per_thread(self._ctx, int(ppt)))
+
+    def set_steps_per_launch(self, steps=0):
+        _check(self._ctx, lib().sde_set_steps_per_launch(self._ctx, int(steps)))
 
     def occupancy(self, block_threads=128):
         b, s = ctypes.c_int(), ctypes.c_int()

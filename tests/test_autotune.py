@@ -1,6 +1,6 @@
-"""The launch-shape autotuner: selection, cache keys and the cache file (CPU),
-and one real tuning on the GPU whose chosen shape reproduces the default's
-results bit for bit."""
+"""The launch autotuner: selection, cache keys and the cache file (CPU), and one
+real tuning on the GPU whose chosen knobs reproduce the default's results bit
+for bit."""
 import json
 
 import pytest
@@ -9,17 +9,21 @@ from paper_1409_4923_gb300 import autotune as AT
 
 
 def test_choose_picks_the_fastest_and_keeps_the_first_on_ties():
-    t = {(128, 0): 1.0, (64, 0): 0.8, (32, 152): 0.8, (96, 304): 1.2}
-    assert AT.choose(t) == (64, 0)
-    assert AT.choose({(128, 0): 1.0, (64, 0): 1.0}) == (128, 0)
+    t = {(128, 0, 1): 1.0, (64, 0, 1): 0.8, (32, 152, 2): 0.8, (96, 304, 1): 1.2}
+    assert AT.choose(t) == (64, 0, 1)
+    assert AT.choose({(128, 0, 1): 1.0, (64, 0, 1): 1.0}) == (128, 0, 1)
+    assert AT.choose({0: 2.0, 1024: 2.5}) == 0
 
 
 def test_candidates_and_keys():
     c = AT.candidates(152)
-    assert (128, 0) in c and (32, 608) in c and len(c) == len(AT.BLOCKS) * len(AT.GRID_MULTIPLES)
+    assert c[0] == (128, 0, 1)                      # the default shape comes first
+    assert (32, 608, 2) in c and len(set(c)) == len(c)
+    assert len(c) == len(AT.BLOCKS) * len(AT.GRID_MULTIPLES) * len(AT.PATHS_PER_THREAD)
     assert AT.size_class(1 << 20) == 10 and AT.size_class(1) == 0
     assert AT.key("GB300", 0, 5, 1 << 20) != AT.key("GB300", 0, 6, 1 << 20)
     assert AT.key("GB300", 0, 5, 1 << 20) == AT.key("GB300", 0, 5, (1 << 20) + 5)
+    assert all(s % 32 == 0 for s in AT.STEPS_PER_LAUNCH) and AT.STEPS_PER_LAUNCH[0] == 0
 
 
 def test_cache_round_trip(tmp_path):
@@ -41,15 +45,17 @@ def test_tune_on_gpu(tmp_path):
     spec = W.run_spec("dichot_2p20")
     prm = E.make_params(**spec["params"])
     cache = str(tmp_path / "tune.json")
-    b, g, t = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, n_probe_steps=512, cache=cache)
-    assert (b, g) in t and len(t) == len(AT.BLOCKS) * len(AT.GRID_MULTIPLES)
+    t = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, n_probe_steps=512, cache=cache)
+    assert (t["block"], t["grid"], t["ppt"]) in t["seconds"]
+    assert len(t["seconds"]) == len(AT.candidates(torch.cuda.get_device_properties(0).multi_processor_count))
+    assert t["steps_per_launch"] in AT.STEPS_PER_LAUNCH
     assert json.load(open(cache))
-    b2, g2, t2 = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, cache=cache)
-    assert (b2, g2) == (b, g) and t2 is None
+    t2 = AT.tune(spec["model"], prm, spec["dt"], 1 << 16, cache=cache)
+    assert t2 == {f: t[f] for f in AT.DEFAULT}
     sums = []
-    for shape in ((128, 0), (b, g)):
+    for knobs in (AT.DEFAULT, t2):
         eng = E.Engine(spec["model"], prm, seed=0)
-        eng.set_tuning(*shape)
+        AT.apply_tuning(eng, knobs)
         eng.run(5000, spec["dt"], 100, 700)
         sums.append(eng.stats()["sums"])
         eng.close()
