@@ -24,7 +24,7 @@ import numpy as np
 from . import build as _build
 
 INERTIAL_WASHBOARD, OVERDAMPED_WASHBOARD, OVERDAMPED_PWL, OVERDAMPED_LINEAR = 0, 1, 2, 3
-GAUSS, POISSON, DICHOT, GAUSS_NORMAL, POIS_COMPENSATED = 1, 2, 4, 8, 16
+GAUSS, POISSON, DICHOT, GAUSS_NORMAL, POIS_COMPENSATED, DICHOT_IN_DRIFT = 1, 2, 4, 8, 16, 32
 
 
 class Params(ctypes.Structure):

@@ -62,7 +62,7 @@ typedef struct {
     uint64_t seed;
     uint32_t path;
     double dt;
-    double G;          /* Gaussian intensity factor, Alg. 2 line 1 */
+    double G;          /* Gaussian intensity factor G of Alg. 2 */
     double aP;         /* bias of the Poisson noise, Eq. 6 (or compensated) */
     double kink_min;   /* PWL force: distance of evaluations to the kinks */
 } orc_ctx;
@@ -135,7 +135,7 @@ static void note_margin(double q, double* margin)
 
 typedef struct { const orc_ctx* c; int64_t s; uint64_t j; double margin; } pois_gen;
 
-/* Waiting time and amplitude of Poisson event j (Alg. 3 lines 4-7). */
+/* Waiting time and amplitude of Poisson event j (the event branch of Alg. 3). */
 static void pois_event(pois_gen* g, uint64_t j, int64_t* wait, double* z)
 {
     const orc_ctx* c = g->c;
@@ -171,7 +171,7 @@ static double pois_step(pois_gen* g)
 
 typedef struct { const orc_ctx* c; int64_t s; uint64_t j; int d; double margin; } dich_gen;
 
-/* Sojourn of event j in the state it enters (Alg. 4 lines 4-5 and 9-10). */
+/* Sojourn of event j in the state it enters (the waiting-time draws of Alg. 4). */
 static int64_t dich_wait(dich_gen* g, uint64_t j, int state)
 {
     const orc_ctx* c = g->c;
@@ -248,29 +248,34 @@ static void run_one(int model, const orc_params* p, uint64_t seed, uint32_t path
         const double t0 = (double)n * dt, t1 = (double)(n + 1) * dt;
         double dxi = (nz & ORC_GAUSS) ? gauss_step(&gg, n) : 0.0;
         double deta = (nz & ORC_POISSON) ? pois_step(&pg) : 0.0;
-        double dgam = (nz & ORC_DICHOT) ? dich_step(&dg) * dt : 0.0;
+        const double gam = (nz & ORC_DICHOT) ? dich_step(&dg) : 0.0;
+        /* Gamma_n enters as the corrector increment Delta Gamma_n = Gamma_n dt
+         * (Algorithm 1), or, with ORC_DICHOT_IN_DRIFT, as a force term of
+         * Eq. 24, constant over the step, in every drift evaluation */
+        const double gdrift = (nz & ORC_DICHOT_IN_DRIFT) ? gam : 0.0;
+        const double dgam = (nz & ORC_DICHOT_IN_DRIFT) ? 0.0 : gam * dt;
 
         if (inertial) {
             /* Algorithm 1 applied to y = (x, v); noise acts on v only and the
              * jump increments enter only the corrector. */
             double F1x = v;
-            double F1v = -p->gamma * v + minus_dV(&c, x) + drive(&c, t0);
+            double F1v = -p->gamma * v + minus_dV(&c, x) + drive(&c, t0) + gdrift;
             double xb = x + F1x * dt;
             double vb = v + F1v * dt + dxi;
             double F2x = vb;
-            double F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1);
+            double F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             xb = x + 0.5 * (F1x + F2x) * dt;                      /* predictor */
             vb = v + 0.5 * (F1v + F2v) * dt + dxi;
             F2x = vb;
-            F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1);
+            F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             x = x + 0.5 * (F1x + F2x) * dt;                       /* corrector */
             v = v + 0.5 * (F1v + F2v) * dt + dxi + deta + dgam;
         } else {
-            double F1 = minus_dV(&c, x) + drive(&c, t0);
+            double F1 = minus_dV(&c, x) + drive(&c, t0) + gdrift;
             double xb = x + F1 * dt + dxi;
-            double F2 = minus_dV(&c, xb) + drive(&c, t1);
+            double F2 = minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             xb = x + 0.5 * (F1 + F2) * dt + dxi;                  /* predictor */
-            F2 = minus_dV(&c, xb) + drive(&c, t1);
+            F2 = minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             x = x + 0.5 * (F1 + F2) * dt + dxi + deta + dgam;     /* corrector */
         }
         if (n + 1 == n_tr) X_i = x;

@@ -23,7 +23,9 @@
  * Noise: Gaussian white (Algorithm 2 three-point law, Eq. 25, or Gaussian
  * increments), white Poissonian (Algorithm 3, Eqs. 3-8, 26-27), dichotomous
  * (Algorithm 4, Eqs. 13-17, 29-30); all enter the velocity of the inertial
- * model and the position of the overdamped ones.
+ * model and the position of the overdamped ones.  The jump increments enter
+ * the corrector only (Algorithm 1); with ORC_DICHOT_IN_DRIFT the dichotomous
+ * force is instead a drift term, constant over the step.
  *
  * Random stream contract (Philox4x32-10 of Salmon et al., SC'11):
  *   key     = (seed & 0xffffffff, seed >> 32)
@@ -59,7 +61,8 @@ enum { ORC_INERTIAL_WASHBOARD = 0, ORC_OVERDAMPED_WASHBOARD = 1,
        ORC_OVERDAMPED_PWL = 2, ORC_OVERDAMPED_LINEAR = 3 };
 
 enum { ORC_GAUSS = 1u, ORC_POISSON = 2u, ORC_DICHOT = 4u,
-       ORC_GAUSS_NORMAL = 8u, ORC_POIS_COMPENSATED = 16u };
+       ORC_GAUSS_NORMAL = 8u, ORC_POIS_COMPENSATED = 16u,
+       ORC_DICHOT_IN_DRIFT = 32u   /* Gamma(t) as a drift term, not a corrector increment */ };
 
 typedef struct {
     double gamma, a, omega, F, Q;

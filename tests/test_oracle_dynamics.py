@@ -133,6 +133,38 @@ def test_overdamped_driven_deterministic(orc):
     assert errs[-1] < 1e-5 and 3.5 < errs[0] / errs[1] < 4.5
 
 
+@pytest.mark.parametrize("model", ["inertial", "linear"])
+def test_dichotomous_force_as_drift_is_second_order(orc, model):
+    """Frozen dichotomous force (rates so small that no flip happens) and no
+    other force: v' = -g v + Gamma (inertial) or x' = -k x + Gamma (linear
+    force) have the closed form y(T) = Gamma/g + (y0 - Gamma/g) e^{-g T}.
+    As a drift term (DICHOT_IN_DRIFT) Gamma is integrated by the
+    predictor-corrector, whose error falls 4x per halving of dt; as Algorithm
+    1's corrector increment it is a first-order splitting (2x).  A term
+    dropped from one of the three drift evaluations, or Gamma counted twice,
+    breaks one of the two rates."""
+    g, b, y0, T = 0.9, 0.5, 1.0, 4.0
+    for flags, lo, hi in ((orc.DICHOT | orc.DICHOT_IN_DRIFT, 3.9, 4.2), (orc.DICHOT, 1.95, 2.05)):
+        errs = []
+        for dt in (0.04, 0.02, 0.01):
+            n = int(round(T / dt))
+            if model == "inertial":
+                p = orc.make_params(gamma=g, V0=0.0, Fa=b, Fb=b, mua=1e-9, mub=1e-9, v0_lo=y0,
+                                    v0_hi=y0, noise=flags)
+                r = orc.run_paths(orc.INERTIAL_WASHBOARD, p, 0, 0, 16, dt, 0, n)
+                y = r["v_f"]
+            else:
+                p = orc.make_params(V0=g, Fa=b, Fb=b, mua=1e-9, mub=1e-9, x0_lo=y0, x0_hi=y0,
+                                    noise=flags)
+                r = orc.run_paths(orc.OVERDAMPED_LINEAR, p, 0, 0, 16, dt, 0, n)
+                y = r["X_f"]
+            assert (r["jD"] == 0).all() and set(r["d"]) == {0, 1}     # frozen, both states seen
+            G = np.where(r["d"] == 1, b, -b)
+            errs.append(np.abs(y - (G / g + (y0 - G / g) * math.exp(-g * T))).max())
+        rates = [errs[i] / errs[i + 1] for i in range(2)]
+        assert all(lo < q < hi for q in rates), (flags, errs)
+
+
 @pytest.mark.parametrize("compensated", [False, True])
 def test_poisson_free_particle(orc, compensated):
     """Overdamped, no force, Poisson only: x_n - x_0 is a sum of n i.i.d. increments
