@@ -20,7 +20,8 @@
  *   SDE_OVERDAMPED_PWL        as the previous line with V of Eq. 2 (Eq. 24;
  *                             Models I and II are its limits, Eqs. 1 and 12)
  * Noise is added to v (inertial) or x (overdamped).  The Poissonian and
- * dichotomous increments enter only the corrector (Algorithm 1 line 6).
+ * dichotomous increments enter only the corrector (Algorithm 1), unless
+ * SDE_DICHOT_IN_DRIFT makes the dichotomous force a drift term.
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit seed,
  * counter = (index_lo, tag << 30 | point, path, index_hi); tag 0 initial
@@ -64,6 +65,10 @@ typedef enum {
 #define SDE_GAUSS_NORMAL      8u   /* Gaussian increments instead of Eq. 25      */
 #define SDE_POIS_COMPENSATED 16u   /* bias a = zeta (1 - e^{-lambda dt}) / dt    */
                                    /* instead of Eq. 6's lambda zeta             */
+#define SDE_DICHOT_IN_DRIFT  32u   /* the dichotomous force Gamma(t) as a drift  */
+                                   /* term in all three drift evaluations of     */
+                                   /* Algorithm 1 instead of a corrector         */
+                                   /* increment; needs SDE_NOISE_DICHOT          */
 
 /* Parameters of one point of parameter space.  Plain old data; the library
  * copies it at the call.  Rates and intensities must be finite and >= 0;

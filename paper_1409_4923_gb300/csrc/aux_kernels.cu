@@ -5,20 +5,20 @@
 namespace sde {
 
 #define SDE_POINT_DECL(M, PPT) \
-cudaError_t launch_point_m##M##_p##PPT(bool, bool, int, const PointConsts&, const LaunchConsts&, \
+cudaError_t launch_point_m##M##_p##PPT(bool, int, int, const PointConsts&, const LaunchConsts&, \
                                       const Workspace&, const PathOutPtrs&, int, int, int, cudaStream_t); \
-int blocks_per_sm_m##M##_p##PPT(bool, bool, int, int);
+int blocks_per_sm_m##M##_p##PPT(bool, int, int, int);
 SDE_POINT_DECL(0, 1) SDE_POINT_DECL(1, 1) SDE_POINT_DECL(2, 1)
 SDE_POINT_DECL(0, 2) SDE_POINT_DECL(1, 2) SDE_POINT_DECL(2, 2)
 #undef SDE_POINT_DECL
 #define SDE_SEG_DECL(M) \
-cudaError_t launch_segment_m##M(bool, bool, int, const PointConsts&, const LaunchConsts&, \
+cudaError_t launch_segment_m##M(bool, int, int, const PointConsts&, const LaunchConsts&, \
                                 const StatePlanes&, uint32_t, uint32_t, const Workspace&, \
                                 const PathOutPtrs&, int, int, int, cudaStream_t);
 SDE_SEG_DECL(0) SDE_SEG_DECL(1) SDE_SEG_DECL(2)
 #undef SDE_SEG_DECL
 
-cudaError_t launch_point(int model, bool pois, bool dich, int gauss, int ppt, const PointConsts& P,
+cudaError_t launch_point(int model, bool pois, int dich, int gauss, int ppt, const PointConsts& P,
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                          int bt, int gb, int sm, cudaStream_t st)
 {
@@ -32,7 +32,7 @@ cudaError_t launch_point(int model, bool pois, bool dich, int gauss, int ppt, co
 #undef SDE_M
 }
 
-cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const PointConsts& P,
+cudaError_t launch_segment(int model, bool pois, int dich, int gauss, const PointConsts& P,
                            const LaunchConsts& K, const StatePlanes& M, uint32_t na, uint32_t nb,
                            const Workspace& ws, const PathOutPtrs& po, int bt, int gb, int sm,
                            cudaStream_t st)
@@ -46,7 +46,7 @@ cudaError_t launch_segment(int model, bool pois, bool dich, int gauss, const Poi
     }
 }
 
-int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int ppt, int bt)
+int point_blocks_per_sm(int model, bool pois, int dich, int gauss, int ppt, int bt)
 {
 #define SDE_M(M) \
     case M: return ppt == 2 ? blocks_per_sm_m##M##_p2(pois, dich, gauss, bt) \
@@ -63,7 +63,7 @@ int point_blocks_per_sm(int model, bool pois, bool dich, int gauss, int ppt, int
 // Persistent scan over (point, 32-path tile) items of the inertial washboard
 // (Sec. 5: many parameter values in one kernel call).  Items are ordered
 // longest first on the host; each warp pulls the next one from the counter.
-template <bool POIS, bool DICH, int GAUSS>
+template <bool POIS, int DICH, int GAUSS>
 __global__ void __launch_bounds__(128) scan_kernel(const PointConsts* __restrict__ pts,
                                                    const uint2* __restrict__ items,
                                                    const __grid_constant__ LaunchConsts K,
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128) scan_kernel(const PointConsts* __restrict
     }
 }
 
-template <bool POIS, bool DICH, int GAUSS>
+template <bool POIS, int DICH, int GAUSS>
 static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, const LaunchConsts& K,
                                  const Workspace& ws, int bt, int gb, int sm, cudaStream_t st)
 {
@@ -105,16 +105,17 @@ static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(bool pois, bool dich, int gauss, const PointConsts* pts, const uint2* items,
+cudaError_t launch_scan(bool pois, int dich, int gauss, const PointConsts* pts, const uint2* items,
                         const LaunchConsts& K, const Workspace& ws, int bt, int gb, int sm,
                         cudaStream_t st)
 {
 #define SDE_SCAN(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) \
         return launch_scan_t<PO, DI, GA>(pts, items, K, ws, bt, gb, sm, st);
-    SDE_SCAN(true, true, kGauss3Point) SDE_SCAN(true, false, kGauss3Point)
-    SDE_SCAN(false, true, kGauss3Point) SDE_SCAN(false, false, kGauss3Point)
-    SDE_SCAN(true, true, 0) SDE_SCAN(true, false, 0) SDE_SCAN(false, true, 0) SDE_SCAN(false, false, 0)
+    SDE_SCAN(true, 1, kGauss3Point) SDE_SCAN(true, 0, kGauss3Point) SDE_SCAN(true, 2, kGauss3Point)
+    SDE_SCAN(false, 1, kGauss3Point) SDE_SCAN(false, 0, kGauss3Point) SDE_SCAN(false, 2, kGauss3Point)
+    SDE_SCAN(true, 1, 0) SDE_SCAN(true, 0, 0) SDE_SCAN(true, 2, 0)
+    SDE_SCAN(false, 1, 0) SDE_SCAN(false, 0, 0) SDE_SCAN(false, 2, 0)
 #undef SDE_SCAN
     return cudaErrorInvalidValue;
 }

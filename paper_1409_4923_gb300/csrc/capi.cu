@@ -151,7 +151,9 @@ int validate_params(sde_ctx* c, sde_model model, const sde_params* p)
     if (!finite_nonneg(p->Q)) return fail(c, SDE_EINVAL, "Q must be >= 0");
     if (model == SDE_INERTIAL_WASHBOARD && !(p->gamma > 0.0))
         return fail(c, SDE_EINVAL, "gamma must be > 0 for the inertial model");
-    if (p->noise_flags & ~31u) return fail(c, SDE_EINVAL, "unknown noise flag");
+    if (p->noise_flags & ~63u) return fail(c, SDE_EINVAL, "unknown noise flag");
+    if ((p->noise_flags & SDE_DICHOT_IN_DRIFT) && !(p->noise_flags & SDE_NOISE_DICHOT))
+        return fail(c, SDE_EINVAL, "SDE_DICHOT_IN_DRIFT needs SDE_NOISE_DICHOT");
     if ((p->noise_flags & SDE_NOISE_POISSON) && !(p->lambda > 0.0 && p->zeta > 0.0))
         return fail(c, SDE_EINVAL, "Poisson noise needs lambda > 0 and zeta > 0");
     if ((p->noise_flags & SDE_NOISE_DICHOT) &&
@@ -172,6 +174,13 @@ int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t 
 }
 
 // Gaussian kernel variant: none (flag off or zero intensity), three-point, Gaussian.
+// Dichotomous kernel variant: none, corrector increment (Algorithm 1), or drift term.
+int dich_kind(uint32_t flags)
+{
+    if (!(flags & SDE_NOISE_DICHOT)) return 0;
+    return (flags & SDE_DICHOT_IN_DRIFT) ? 2 : 1;
+}
+
 int gauss_kind(const sde_params& p)
 {
     if (!(p.noise_flags & SDE_NOISE_GAUSS) || !(p.Q > 0.0)) return 0;
@@ -427,7 +436,7 @@ int sde_occupancy(sde_ctx* c, int block_threads, int* blocks_per_sm, int* sm_cou
     if (!c || !blocks_per_sm || !sm_count) return SDE_EINVAL;
     const uint32_t f = c->p.noise_flags;
     *blocks_per_sm = point_blocks_per_sm((int)c->model, (f & SDE_NOISE_POISSON) != 0,
-                                         (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p),
+                                         dich_kind(f), gauss_kind(c->p),
                                          c->paths_per_thread, block_threads);
     *sm_count = c->sm_count;
     return SDE_OK;
@@ -460,7 +469,7 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
     const uint32_t f = c->p.noise_flags;
     const uint64_t total = n_tr + n_avg;
     if (c->steps_per_launch == 0 || c->steps_per_launch >= total) {
-        SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+        SDE_CUDA(c, launch_point((int)c->model, (f & SDE_NOISE_POISSON) != 0, dich_kind(f),
                                  gauss_kind(c->p), c->paths_per_thread, P, K, ws, po, c->block_threads,
                                  c->grid_blocks, c->sm_count, c->stream));
     } else {
@@ -483,7 +492,7 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
             const uint64_t nb = std::min(total, na + c->steps_per_launch);
             if (na > 0) SDE_CUDA(c, cudaMemsetAsync(base, 0, 4, c->stream));
             SDE_CUDA(c, launch_segment((int)c->model, (f & SDE_NOISE_POISSON) != 0,
-                                       (f & SDE_NOISE_DICHOT) != 0, gauss_kind(c->p), P, K, M,
+                                       dich_kind(f), gauss_kind(c->p), P, K, M,
                                        (uint32_t)na, (uint32_t)nb, ws, po, c->block_threads,
                                        c->grid_blocks, c->sm_count, c->stream));
         }
@@ -588,7 +597,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             if (capture) SDE_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaMemsetAsync(base, 0, 8, c->stream);
             if (e == cudaSuccess)
-                e = launch_scan((flags & SDE_NOISE_POISSON) != 0, (flags & SDE_NOISE_DICHOT) != 0,
+                e = launch_scan((flags & SDE_NOISE_POISSON) != 0, dich_kind(flags),
                                 (flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0, d_pts,
                                 d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream);
             if (e == cudaSuccess) e = launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream);
@@ -622,7 +631,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * ranges[i].x};
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (flags & SDE_NOISE_POISSON) != 0,
-                                     (flags & SDE_NOISE_DICHOT) != 0, gauss_kind(pts[i].p),
+                                     dich_kind(flags), gauss_kind(pts[i].p),
                                      c->paths_per_thread, P[i], K, wsi,
                                      po, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
@@ -679,7 +688,7 @@ int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)
     SDE_CUDA(c, cudaMemsetAsync(ws.status, 0, 4, c->stream));
     if (S.scan_kernel) {
         const LaunchConsts K = make_launch(c->seed, S.total_items, budget);
-        SDE_CUDA(c, launch_scan((S.flags & SDE_NOISE_POISSON) != 0, (S.flags & SDE_NOISE_DICHOT) != 0,
+        SDE_CUDA(c, launch_scan((S.flags & SDE_NOISE_POISSON) != 0, dich_kind(S.flags),
                                 (S.flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0,
                                 (const PointConsts*)(base + S.off_pts), (const uint2*)(base + S.off_items),
                                 K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
@@ -690,7 +699,7 @@ int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)
             Workspace wsi{d_counters + i, ws.status, ws.partials + 5ull * S.ranges[i].x};
             PathOutPtrs po{nullptr, nullptr, nullptr, nullptr, nullptr};
             SDE_CUDA(c, launch_point((int)c->model, (S.flags & SDE_NOISE_POISSON) != 0,
-                                     (S.flags & SDE_NOISE_DICHOT) != 0, S.gauss[i], c->paths_per_thread,
+                                     dich_kind(S.flags), S.gauss[i], c->paths_per_thread,
                                      S.P[i], K, wsi, po,
                                      c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
@@ -779,7 +788,7 @@ int sde_advance(sde_ctx* c, uint64_t n_steps, const sde_path_out* out, uint64_t*
     const LaunchConsts K = make_launch(r.seed, r.items, 0);
     const StatePlanes M{(unsigned char*)c->state, r.stride};
     const uint32_t f = r.p.noise_flags;
-    SDE_CUDA(c, launch_segment((int)c->model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+    SDE_CUDA(c, launch_segment((int)c->model, (f & SDE_NOISE_POISSON) != 0, dich_kind(f),
                                gauss_kind(r.p), P, K, M, (uint32_t)na, (uint32_t)nb, ws, po,
                                c->block_threads, c->grid_blocks, c->sm_count, c->stream));
     if (last) {

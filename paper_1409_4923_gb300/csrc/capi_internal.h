@@ -18,6 +18,7 @@ int validate_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t 
 
 // Kernel template of the Gaussian noise: 0 (none), three-point or Gaussian.
 int gauss_kind(const sde_params& p);
+int dich_kind(uint32_t flags);
 
 // FP32/FP64 kernel constants of one point and of one launch.
 int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,

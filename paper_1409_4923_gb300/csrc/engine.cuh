@@ -206,12 +206,28 @@ __device__ __forceinline__ void accumulate(PathState& S)
     }
 }
 
-// One step of Algorithm 1.  dxi: Gaussian increment; jump: Poissonian plus
-// dichotomous increment (corrector only); d0 / d1: drive x dt at t_n, t_{n+1}.
-template <int MODEL, bool ACC, bool FOLD>
-__device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, float dxi,
-                                        float jump, float d0, float d1)
+// h1 plus the corrector's jump increments: the Poissonian pj, and the
+// dichotomous dg unless it is part of the drift (DICH == 2).
+template <bool POIS, int DICH>
+__device__ __forceinline__ float with_jumps(float h1, float pj, float dg)
 {
+    if (DICH == 1) return POIS ? h1 + (pj + dg) : h1 + dg;
+    return POIS ? h1 + pj : h1;
+}
+
+// One step of Algorithm 1.  dxi: Gaussian increment; pj: Poissonian
+// increment; dg: dichotomous increment Gamma_n dt; d0 / d1: drive x dt at
+// t_n, t_{n+1}.  The jump increments enter the corrector only (Algorithm 1);
+// with DICH == 2 the dichotomous force is instead a drift term, constant over
+// the step, in all three drift evaluations.
+template <int MODEL, bool POIS, int DICH, bool ACC, bool FOLD>
+__device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, float dxi, float pj,
+                                        float dg, float d0, float d1)
+{
+    if (DICH == 2) {
+        d0 += dg;
+        d1 += dg;
+    }
     if (MODEL == kModelInertial) {
         const float b1 = add_force_dt<MODEL>(fmaf(-P.gdt, S.v, d0), S.c, P);   // F1_v dt
         const float vxi = S.v + dxi;
@@ -224,7 +240,7 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         vb = fmaf(0.5f, b2, h1);                                            // predictor v
         const float b3 = add_force_dt<MODEL>(fmaf(-P.gdt, vb, d1), cb, P);
         S.c = fmaf(P.whdt, vb, ch);                                         // corrector x
-        S.v = fmaf(0.5f, b3, h1 + jump);                                    // corrector v
+        S.v = fmaf(0.5f, b3, with_jumps<POIS, DICH>(h1, pj, dg));           // corrector v
         accumulate<ACC>(S);
     } else {
         const float b1 = add_force_dt<MODEL>(d0, S.c, P);
@@ -234,7 +250,7 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         const float h1 = fmaf(0.5f, b1, cxi);
         cb = fmaf(0.5f, b2, h1);                                            // predictor
         const float b3 = add_force_dt<MODEL>(d1, cb, P);
-        S.c = fmaf(0.5f, b3, h1 + jump);                                    // corrector
+        S.c = fmaf(0.5f, b3, with_jumps<POIS, DICH>(h1, pj, dg));           // corrector
     }
     if (FOLD) fold<MODEL>(S);
 }
@@ -275,21 +291,21 @@ __device__ __forceinline__ void dich_event(PathState& S, const PointConsts& P,
     S.JD += 1u;
 }
 
-// Jump increment of step n with the events drawn as they happen.
-template <bool POIS, bool DICH>
-__device__ __forceinline__ float jump_inline(PathState& S, const PointConsts& P, const LaunchConsts& K,
-                                             uint32_t path, uint32_t n)
+// Jump increments of step n with the events drawn as they happen.
+template <bool POIS, int DICH>
+__device__ __forceinline__ void jumps_inline(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                             uint32_t path, uint32_t n, float& pj, float& dg)
 {
-    float j = 0.0f;
+    pj = 0.0f;
+    dg = 0.0f;
     if (POIS) {
-        j = -P.aP_dt;
-        if (n == S.eP) j = pois_event(S, P, K, path);
+        pj = -P.aP_dt;
+        if (n == S.eP) pj = pois_event(S, P, K, path);
     }
     if (DICH) {
         if (n == S.eD) dich_event(S, P, K, path);
-        j += S.dst ? P.Fb_dt : P.mFa_dt;
+        dg = S.dst ? P.Fb_dt : P.mFa_dt;
     }
-    return j;
 }
 
 // Events of the chunk [n0, n0 + 32), drawn before it is integrated so that
@@ -299,7 +315,7 @@ __device__ __forceinline__ float jump_inline(PathState& S, const PointConsts& P,
 // step n0 + i.  Returns false (and restores the Poisson state) when some lane
 // of the warp has more than three kicks in the chunk: the warp then takes the
 // Poisson events of this chunk inline.  All 32 lanes must call this together.
-template <bool POIS, bool DICH>
+template <bool POIS, int DICH>
 __device__ __forceinline__ bool chunk_events(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                              uint32_t path, uint32_t n0, uint32_t& pm, float& z0,
                                              float& z1, float& z2, uint32_t& dm)
@@ -368,7 +384,7 @@ __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const Poi
 
 // Steps n in [n, n_end) one at a time (phase edges that are not whole
 // 32-step chunks).
-template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                              uint32_t path, uint32_t n, uint32_t n_end)
 {
@@ -385,8 +401,9 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
             const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
             dxi = gauss_inc<GAUSS>(w, n & 3u, P);
         }
-        const float jump = jump_inline<POIS, DICH>(S, P, K, path, n);
-        pc_step<MODEL, ACC, true>(S, P, dxi, jump, drive_at(n, P), drive_at(n + 1u, P));
+        float pj, dg;
+        jumps_inline<POIS, DICH>(S, P, K, path, n, pj, dg);
+        pc_step<MODEL, POIS, DICH, ACC, true>(S, P, dxi, pj, dg, drive_at(n, P), drive_at(n + 1u, P));
     }
 }
 
@@ -398,7 +415,7 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 // first block (group); each block (group) draws the next one's words while it
 // integrates, so the Philox multiplies interleave with the step arithmetic,
 // and w returns holding those that follow the chunk.
-template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST>
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST>
 __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                             uint32_t path, uint32_t n0, float dch, float& dcur,
                                             uint4& w, uint32_t pm, float z0, float z1, float z2,
@@ -424,20 +441,20 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
             float dxi = 0.0f;
             if (GAUSS == kGauss3Point) dxi = three_point(r, P);
             else if (GAUSS == kGaussNormal) dxi = gauss_inc<GAUSS>(w, k, P);
-            float jump = 0.0f;
+            float pj = 0.0f, dg = 0.0f;
             if (POIS) {
                 if (FAST) {
                     const bool kick = (pm & (1u << k)) != 0u;
-                    jump = kick ? z0 : -P.aP_dt;
+                    pj = kick ? z0 : -P.aP_dt;
                     z0 = kick ? z1 : z0;
                     z1 = kick ? z2 : z1;
                 } else {
-                    jump = -P.aP_dt;
-                    if (n0 + g * 4u + k == S.eP) jump = pois_event(S, P, K, path);
+                    pj = -P.aP_dt;
+                    if (n0 + g * 4u + k == S.eP) pj = pois_event(S, P, K, path);
                 }
             }
-            if (DICH) jump += (dm & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
-            pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, jump, dcur, dnext);
+            if (DICH) dg = (dm & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
+            pc_step<MODEL, POIS, DICH, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, pj, dg, dcur, dnext);
             dcur = dnext;
         }
         if (GAUSS == kGaussNormal || (GAUSS == kGauss3Point && (g & 3u) == 3u)) w = wn;
@@ -453,7 +470,7 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
 // Chunks and flushes sit at absolute step positions, so a run cut into
 // segments at multiples of 32 steps takes the same arithmetic as one launch.
 // All 32 lanes of the warp must call this together.
-template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC>
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC>
 __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                           uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
 {
@@ -489,7 +506,7 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
     if (n < n_end) single_steps<MODEL, POIS, DICH, GAUSS, ACC>(S, P, K, path, n, n_end);
 }
 
-template <int MODEL, bool POIS, bool DICH>
+template <int MODEL, bool POIS, int DICH>
 __device__ __forceinline__ void init_path(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                           uint32_t path)
 {
@@ -526,7 +543,7 @@ struct PathResult {
 };
 
 // Eq. 31 summand and the path's other results from its final state.
-template <int MODEL, bool POIS, bool DICH>
+template <int MODEL, bool POIS, int DICH>
 __device__ __forceinline__ void finish_path(const PathState& S, const PointConsts& P, PathResult& R)
 {
     const double dX = __fma_rn((double)S.kf - (double)S.kf_i, P.period,
@@ -540,7 +557,7 @@ __device__ __forceinline__ void finish_path(const PathState& S, const PointConst
     R.jD = DICH ? S.JD - 1u : 0u;
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, int DICH, int GAUSS>
 __device__ __forceinline__ void simulate_path(const PointConsts& P, const LaunchConsts& K,
                                               uint32_t path, uint32_t lane, PathResult& R)
 {
@@ -559,7 +576,7 @@ __device__ __forceinline__ void simulate_path(const PointConsts& P, const Launch
 // transient in the segment, the snapshot at t_i if the transient ends in it,
 // then the part of the averaging window.  Cut points at multiples of 32 steps
 // (or at n_transient) give the arithmetic of simulate_path exactly.
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, int DICH, int GAUSS>
 __device__ __forceinline__ void advance_path(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                              uint32_t path, uint32_t lane, uint32_t na, uint32_t nb)
 {
@@ -584,7 +601,7 @@ __device__ __forceinline__ void advance_path(PathState& S, const PointConsts& P,
 // of some path takes all paths' events inline, which gives the same values),
 // so results do not depend on PPT.
 
-template <bool POIS, bool DICH, int PPT>
+template <bool POIS, int DICH, int PPT>
 __device__ __forceinline__ bool chunk_events_multi(PathState (&S)[PPT], const PointConsts& P,
                                                    const LaunchConsts& K, const uint32_t (&path)[PPT],
                                                    uint32_t n0, uint32_t (&pm)[PPT], float (&z0)[PPT],
@@ -630,7 +647,7 @@ __device__ __forceinline__ bool chunk_events_multi(PathState (&S)[PPT], const Po
     return true;
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, bool FAST, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST, int PPT>
 __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const PointConsts& P,
                                                   const LaunchConsts& K, const uint32_t (&path)[PPT],
                                                   uint32_t n0, float dch, float& dcur, uint4 (&w)[PPT],
@@ -660,20 +677,21 @@ __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const Poi
                 float dxi = 0.0f;
                 if (GAUSS == kGauss3Point) dxi = three_point(r[p], P);
                 else if (GAUSS == kGaussNormal) dxi = gauss_inc<GAUSS>(w[p], k, P);
-                float jump = 0.0f;
+                float pj = 0.0f, dg = 0.0f;
                 if (POIS) {
                     if (FAST) {
                         const bool kick = (pm[p] & (1u << k)) != 0u;
-                        jump = kick ? z0[p] : -P.aP_dt;
+                        pj = kick ? z0[p] : -P.aP_dt;
                         z0[p] = kick ? z1[p] : z0[p];
                         z1[p] = kick ? z2[p] : z1[p];
                     } else {
-                        jump = -P.aP_dt;
-                        if (n0 + g * 4u + k == S[p].eP) jump = pois_event(S[p], P, K, path[p]);
+                        pj = -P.aP_dt;
+                        if (n0 + g * 4u + k == S[p].eP) pj = pois_event(S[p], P, K, path[p]);
                     }
                 }
-                if (DICH) jump += (dm[p] & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
-                pc_step<MODEL, ACC, FoldPerStep<MODEL>::value>(S[p], P, dxi, jump, dcur, dnext);
+                if (DICH) dg = (dm[p] & (1u << k)) != 0u ? P.Fb_dt : P.mFa_dt;
+                pc_step<MODEL, POIS, DICH, ACC, FoldPerStep<MODEL>::value>(S[p], P, dxi, pj, dg, dcur,
+                                                                           dnext);
             }
             dcur = dnext;
         }
@@ -687,7 +705,7 @@ __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const Poi
     }
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS, bool ACC, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, int PPT>
 __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const PointConsts& P,
                                                 const LaunchConsts& K, const uint32_t (&path)[PPT],
                                                 uint32_t lane, uint32_t n, uint32_t n_end)
@@ -737,7 +755,7 @@ __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const Point
     }
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 __device__ __forceinline__ void simulate_paths(const PointConsts& P, const LaunchConsts& K,
                                                const uint32_t (&path)[PPT], uint32_t lane,
                                                PathResult (&R)[PPT])

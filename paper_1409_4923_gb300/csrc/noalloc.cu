@@ -92,7 +92,7 @@ extern "C" int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t se
     noalloc_begin<<<1, 1, 0, st>>>(ws.counter, ws.status, range, items);
     e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = launch_point((int)model, (f & SDE_NOISE_POISSON) != 0, (f & SDE_NOISE_DICHOT) != 0,
+        e = launch_point((int)model, (f & SDE_NOISE_POISSON) != 0, dich_kind(f),
                          gauss_kind(*p), 1, P, K, ws, po, 128, 0, sm_count, st);
     if (e == cudaSuccess) e = launch_fold(ws.partials, range, 1, out5, st);
     if (e == cudaSuccess && status_out) {

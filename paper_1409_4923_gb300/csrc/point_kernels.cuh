@@ -8,7 +8,7 @@ namespace sde {
 // 32-path items (PPT consecutive items at a time, one path of each per lane),
 // integrates its lanes' paths for n_transient + n_avg steps and writes each
 // item's FP64 partial sums (and, optionally, per-path results).
-template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 __global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ PointConsts P,
                                                     const __grid_constant__ LaunchConsts K,
                                                     uint32_t* __restrict__ counter,
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ Poin
     }
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Workspace& ws,
                            const PathOutPtrs& po, int block_threads, int grid_blocks,
                            int sm_count, cudaStream_t st)
@@ -66,7 +66,7 @@ cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Wo
     return cudaGetLastError();
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS, int PPT>
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 int blocks_per_sm_t(int block_threads)
 {
     int per_sm = 0;
@@ -78,47 +78,37 @@ int blocks_per_sm_t(int block_threads)
 // Dispatch over the noise switches for one model and paths-per-lane count
 // (each pair instantiated in its own translation unit).
 template <int MODEL, int PPT>
-cudaError_t launch_point_model(bool pois, bool dich, int gauss, const PointConsts& P,
+cudaError_t launch_point_model(bool pois, int dich, int gauss, const PointConsts& P,
                                const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,
                                int bt, int gb, int sm, cudaStream_t st)
 {
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) \
         return launch_point_t<MODEL, PO, DI, GA, PPT>(P, K, ws, po, bt, gb, sm, st);
-    SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
-    SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
-    SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
-    SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
-    SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
-    SDE_CASE(false, true, kGaussNormal) SDE_CASE(true, true, kGaussNormal)
+    SDE_FOR_EACH_VARIANT(SDE_CASE)
 #undef SDE_CASE
     return cudaErrorInvalidValue;
 }
 
 template <int MODEL, int PPT>
-int blocks_per_sm_model(bool pois, bool dich, int gauss, int bt)
+int blocks_per_sm_model(bool pois, int dich, int gauss, int bt)
 {
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) return blocks_per_sm_t<MODEL, PO, DI, GA, PPT>(bt);
-    SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
-    SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
-    SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
-    SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
-    SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
-    SDE_CASE(false, true, kGaussNormal) SDE_CASE(true, true, kGaussNormal)
+    SDE_FOR_EACH_VARIANT(SDE_CASE)
 #undef SDE_CASE
     return 0;
 }
 
 // Instantiation unit of one (model, paths per lane) pair.
 #define SDE_POINT_UNIT(M, PPT) \
-    cudaError_t launch_point_m##M##_p##PPT(bool pois, bool dich, int gauss, const PointConsts& P, \
+    cudaError_t launch_point_m##M##_p##PPT(bool pois, int dich, int gauss, const PointConsts& P, \
                                           const LaunchConsts& K, const Workspace& ws, \
                                           const PathOutPtrs& po, int bt, int gb, int sm, cudaStream_t st) \
     { \
         return launch_point_model<M, PPT>(pois, dich, gauss, P, K, ws, po, bt, gb, sm, st); \
     } \
-    int blocks_per_sm_m##M##_p##PPT(bool pois, bool dich, int gauss, int bt) \
+    int blocks_per_sm_m##M##_p##PPT(bool pois, int dich, int gauss, int bt) \
     { \
         return blocks_per_sm_model<M, PPT>(pois, dich, gauss, bt); \
     }

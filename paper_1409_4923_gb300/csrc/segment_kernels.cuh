@@ -9,7 +9,7 @@ namespace sde {
 // over steps [na, nb) and saves it.  The segment that ends the run also
 // writes the item's FP64 partial sums (and, optionally, per-path results), so
 // the fold that follows gives the statistics of sde_run.
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, int DICH, int GAUSS>
 __global__ void __launch_bounds__(128) segment_kernel(const __grid_constant__ PointConsts P,
                                                       const __grid_constant__ LaunchConsts K,
                                                       const StatePlanes M, uint32_t na, uint32_t nb,
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128) segment_kernel(const __grid_constant__ Po
     }
 }
 
-template <int MODEL, bool POIS, bool DICH, int GAUSS>
+template <int MODEL, bool POIS, int DICH, int GAUSS>
 cudaError_t launch_segment_t(const PointConsts& P, const LaunchConsts& K, const StatePlanes& M,
                              uint32_t na, uint32_t nb, const Workspace& ws, const PathOutPtrs& po,
                              int block_threads, int grid_blocks, int sm_count, cudaStream_t st)
@@ -60,7 +60,7 @@ cudaError_t launch_segment_t(const PointConsts& P, const LaunchConsts& K, const 
 }
 
 template <int MODEL>
-cudaError_t launch_segment_model(bool pois, bool dich, int gauss, const PointConsts& P,
+cudaError_t launch_segment_model(bool pois, int dich, int gauss, const PointConsts& P,
                                  const LaunchConsts& K, const StatePlanes& M, uint32_t na,
                                  uint32_t nb, const Workspace& ws, const PathOutPtrs& po, int bt,
                                  int gb, int sm, cudaStream_t st)
@@ -68,12 +68,7 @@ cudaError_t launch_segment_model(bool pois, bool dich, int gauss, const PointCon
 #define SDE_CASE(PO, DI, GA) \
     if (pois == PO && dich == DI && gauss == GA) \
         return launch_segment_t<MODEL, PO, DI, GA>(P, K, M, na, nb, ws, po, bt, gb, sm, st);
-    SDE_CASE(false, false, 0) SDE_CASE(true, false, 0)
-    SDE_CASE(false, true, 0) SDE_CASE(true, true, 0)
-    SDE_CASE(false, false, kGauss3Point) SDE_CASE(true, false, kGauss3Point)
-    SDE_CASE(false, true, kGauss3Point) SDE_CASE(true, true, kGauss3Point)
-    SDE_CASE(false, false, kGaussNormal) SDE_CASE(true, false, kGaussNormal)
-    SDE_CASE(false, true, kGaussNormal) SDE_CASE(true, true, kGaussNormal)
+    SDE_FOR_EACH_VARIANT(SDE_CASE)
 #undef SDE_CASE
     return cudaErrorInvalidValue;
 }

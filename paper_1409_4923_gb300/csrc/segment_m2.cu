@@ -3,7 +3,7 @@
 
 namespace sde {
 
-cudaError_t launch_segment_m2(bool pois, bool dich, int gauss, const PointConsts& P,
+cudaError_t launch_segment_m2(bool pois, int dich, int gauss, const PointConsts& P,
                               const LaunchConsts& K, const StatePlanes& M, uint32_t na, uint32_t nb,
                               const Workspace& ws, const PathOutPtrs& po, int bt, int gb, int sm,
                               cudaStream_t st)

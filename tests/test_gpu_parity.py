@@ -67,12 +67,19 @@ def _cases(W):
         "pwl-model-I-II": (2, dict(pois, V0=1.0, a=0.0, F=0.0, Q=0.01, zeta=0.667, Fa=3.0, Fb=1.1,
                                    mua=1.0, mub=0.3667, x0_lo=-1.0, x0_hi=1.0, noise_flags=7,
                                    **{"lambda": 2.25}), 0.001),
+        # the dichotomous force as a drift term (SDE_DICHOT_IN_DRIFT)
+        "inertial-dichot-drift": (0, dict(dich, noise_flags=1 | 4 | 32), W.period_steps(4.9, 200)),
+        "inertial-all-drift": (0, dict(both, noise_flags=7 | 32), W.period_steps(4.9, 100)),
+        "pwl-model-II-drift": (2, dict(pois, V0=1.0, a=0.0, F=0.0, Q=0.01, Fa=3.0, Fb=1.1, mua=1.0,
+                                       mub=0.3667, x0_lo=-1.0, x0_hi=1.0, noise_flags=1 | 4 | 32),
+                               0.001),
     }
 
 
 @pytest.mark.parametrize("case", ["inertial-poisson", "inertial-dichot", "inertial-all-noises",
                                   "inertial-gauss-normal", "inertial-compensated",
-                                  "overdamped-washboard", "pwl-model-I-II"])
+                                  "overdamped-washboard", "pwl-model-I-II", "inertial-dichot-drift",
+                                  "inertial-all-drift", "pwl-model-II-drift"])
 @pytest.mark.parametrize("n_tr,n_avg", [(0, 32), (37, 27), (5, 59), (0, 64)])
 def test_per_path_short_horizon(E, W, orc, case, n_tr, n_avg):
     model, prm, dt = _cases(W)[case]
@@ -156,6 +163,20 @@ def test_models_against_oracle_ensemble(E, W, orc):
     prm = dict(Fa=Fa, Fb=Fb, mua=mua, mub=mub, x0_lo=-1.0, x0_hi=1.0, noise_flags=4)
     g_st, _ = gc.engine_run(E, torch, 2, prm, 0, 8192, dt, n // 10, n - n // 10, per_path=False)
     assert abs(g_st["mean_v"] - cf.eq21b_velocity(Fa, Fb, tau)) < 4 * g_st["stderr_v"] + 0.005
+
+
+@pytest.mark.parametrize("case", ["inertial-dichot-drift", "pwl-model-II-drift"])
+def test_dichotomous_drift_ensemble(E, W, orc, case):
+    """Ensemble parity of the drift variant over a long horizon (22,000 steps),
+    with the dichotomous flips bit-exact."""
+    model, prm, dt = _cases(W)[case]
+    paths, n_tr, n_avg = 2048, 2000, 20000
+    g_st, g = gc.engine_run(E, torch, model, prm, 6, paths, dt, n_tr, n_avg)
+    r = orc.run_paths(model, gc.oracle_params(orc, prm), 6, 0, paths, dt, n_tr, n_avg)
+    o = orc.stats(r, n_avg)
+    assert abs(g_st["mean_v"] - o["mean_v"]) <= gc.combined_tol(g_st, o)
+    ok, n_excl = gc.events_equal(g, r)
+    assert ok and n_excl <= 2
 
 
 def test_launch_shape_does_not_change_results(E, W):

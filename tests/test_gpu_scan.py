@@ -39,7 +39,7 @@ def _points(E, W, flags=None):
     return pts
 
 
-@pytest.mark.parametrize("flags", [None, 5, 7])
+@pytest.mark.parametrize("flags", [None, 5, 7, 5 | 32])
 def test_scan_equals_single_runs(E, W, flags):
     """Each point of a scan gives exactly (bitwise) the sums of its own run."""
     pts = _points(E, W, flags)

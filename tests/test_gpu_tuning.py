@@ -31,6 +31,7 @@ def _cases(W):
         (0, dict(both, noise_flags=3), W.period_steps(4.9, 100)),
         (0, dict(both, noise_flags=1 | 2 | 8), W.period_steps(4.9, 100)),
         (0, dict(both, noise_flags=6), W.period_steps(4.9, 100)),
+        (0, dict(both, noise_flags=7 | 32), W.period_steps(4.9, 100)),
         (1, dict(pois, V0=0.2, a=0.5, Q=0.05, Fa=0.3, Fb=0.6, mua=2.0, mub=1.0, noise_flags=7), 0.002),
         (2, dict(pois, V0=1.0, a=0.0, F=0.0, Q=0.01, zeta=0.667, Fa=3.0, Fb=1.1, mua=1.0,
                  mub=0.3667, x0_lo=-1.0, x0_hi=1.0, noise_flags=7, **{"lambda": 2.25}), 0.001),
@@ -62,7 +63,7 @@ def _same(a, b):
         assert np.array_equal(a[1][k], b[1][k]), k
 
 
-@pytest.mark.parametrize("idx", range(7))
+@pytest.mark.parametrize("idx", range(8))
 @pytest.mark.parametrize("paths", [1, 33, 1000, 2048 + 32])   # 1 and 33 items: an odd item count
 def test_two_paths_per_lane_is_bit_identical(E, W, idx, paths):
     model, prm, dt = _cases(W)[idx]
@@ -79,7 +80,7 @@ def test_two_paths_per_lane_any_launch_shape(E, W):
 
 @pytest.mark.parametrize("spl", [32, 96, 1024])
 def test_steps_per_launch_is_bit_identical(E, W, spl):
-    for model, prm, dt in _cases(W)[::2]:
+    for model, prm, dt in _cases(W)[::2] + _cases(W)[5:6]:
         ref = _run(E, model, prm, 1000, dt, 100, 900)
         _same(_run(E, model, prm, 1000, dt, 100, 900, spl=spl), ref)
 
