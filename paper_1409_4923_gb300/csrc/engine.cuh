@@ -421,8 +421,38 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
                                             uint4& w, uint32_t pm, float z0, float z1, float z2,
                                             uint32_t dm)
 {
-    // two groups per iteration unless the Poisson queue doubles the body
-    // (measured: the unrolled two-variant Poisson chunk runs 15 % slower)
+    // Without Box-Muller words the chunk is two 16-step blocks of one Philox
+    // call each: the block's four groups are unrolled, so each group's word
+    // and each step's event bit are compile-time selections.  (The Poisson
+    // queue doubles the step body; there the loop keeps one group per
+    // iteration: measured, the unrolled two-variant Poisson chunk runs 15 %
+    // slower.)
+    constexpr bool kBlockLoop = GAUSS != kGaussNormal && !POIS;
+    if (kBlockLoop) {
+#pragma unroll 1
+        for (uint32_t b = 0; b < 2u; ++b) {
+            uint4 wn = make_uint4(0u, 0u, 0u, 0u);
+            if (GAUSS == kGauss3Point) wn = stream(K, P.c1_gauss, path, (n0 >> 4) + b + 1u);
+#pragma unroll
+            for (uint32_t q = 0; q < 4u; ++q) {
+                uint32_t r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
+#pragma unroll
+                for (uint32_t k = 0; k < 4u; ++k) {
+                    const float dnext = __shfl_sync(0xffffffffu, dch, (int)(b * 16u + q * 4u + k));
+                    const float dxi = GAUSS == kGauss3Point ? three_point(r, P) : 0.0f;
+                    float dg = 0.0f;
+                    if (DICH) dg = (dm & (1u << (q * 4u + k))) != 0u ? P.Fb_dt : P.mFa_dt;
+                    pc_step<MODEL, POIS, DICH, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, 0.0f, dg, dcur,
+                                                                               dnext);
+                    dcur = dnext;
+                }
+                if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
+            }
+            w = wn;
+            dm >>= 16;
+        }
+        return;
+    }
     constexpr int kGroupUnroll = POIS ? 1 : 2;
     uint4 wn = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll kGroupUnroll
