@@ -423,11 +423,10 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
 {
     // Without Box-Muller words the chunk is two 16-step blocks of one Philox
     // call each: the block's four groups are unrolled, so each group's word
-    // and each step's event bit are compile-time selections.  (The Poisson
-    // queue doubles the step body; there the loop keeps one group per
-    // iteration: measured, the unrolled two-variant Poisson chunk runs 15 %
-    // slower.)
-    constexpr bool kBlockLoop = GAUSS != kGaussNormal && !POIS;
+    // and each step's event bit are compile-time selections.  The rare chunks
+    // whose Poisson events take the inline path keep the compact loop of one
+    // group per iteration below.
+    constexpr bool kBlockLoop = GAUSS != kGaussNormal && (!POIS || FAST);
     if (kBlockLoop) {
 #pragma unroll 1
         for (uint32_t b = 0; b < 2u; ++b) {
@@ -440,15 +439,22 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
                 for (uint32_t k = 0; k < 4u; ++k) {
                     const float dnext = __shfl_sync(0xffffffffu, dch, (int)(b * 16u + q * 4u + k));
                     const float dxi = GAUSS == kGauss3Point ? three_point(r, P) : 0.0f;
-                    float dg = 0.0f;
+                    float pj = 0.0f, dg = 0.0f;
+                    if (POIS) {
+                        const bool kick = (pm & (1u << (q * 4u + k))) != 0u;
+                        pj = kick ? z0 : -P.aP_dt;
+                        z0 = kick ? z1 : z0;
+                        z1 = kick ? z2 : z1;
+                    }
                     if (DICH) dg = (dm & (1u << (q * 4u + k))) != 0u ? P.Fb_dt : P.mFa_dt;
-                    pc_step<MODEL, POIS, DICH, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, 0.0f, dg, dcur,
+                    pc_step<MODEL, POIS, DICH, ACC, FoldPerStep<MODEL>::value>(S, P, dxi, pj, dg, dcur,
                                                                                dnext);
                     dcur = dnext;
                 }
                 if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
             }
             w = wn;
+            pm >>= 16;
             dm >>= 16;
         }
         return;
