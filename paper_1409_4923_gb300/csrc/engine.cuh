@@ -437,7 +437,7 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
                 uint32_t r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
 #pragma unroll
                 for (uint32_t k = 0; k < 4u; ++k) {
-                    const float dnext = __shfl_sync(0xffffffffu, dch, (int)(b * 16u + q * 4u + k));
+                    const float dnext = __shfl_sync(0xffffffffu, dch, (int)(q * 4u + k));
                     const float dxi = GAUSS == kGauss3Point ? three_point(r, P) : 0.0f;
                     float pj = 0.0f, dg = 0.0f;
                     if (POIS) {
@@ -456,6 +456,7 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
             w = wn;
             pm >>= 16;
             dm >>= 16;
+            dch = __shfl_down_sync(0xffffffffu, dch, 16);   // the second block's drive values
         }
         return;
     }
