@@ -18,8 +18,11 @@
 #include "sde.h"
 #include "sde_mlp.h"
 
-cudaError_t sde_tc_silu_layer(const __nv_bfloat16* A, int M, const __nv_bfloat16* W, const float* bias,
-                              __nv_bfloat16* out, int* error, int sm_count, cudaStream_t st);
+cudaError_t sde_tc_forward(int M, const float* x, const float* maps, uint32_t log_mask,
+                           const __nv_bfloat16* W1, const float* b1, const __nv_bfloat16* W2,
+                           const float* b2, const __nv_bfloat16* W3, const float* b3,
+                           const __nv_bfloat16* W4, const float* b4, __nv_bfloat16* h2, float* y,
+                           int* error, int sm_count, cudaStream_t st);
 
 namespace {
 
@@ -377,7 +380,7 @@ struct sde_mlp {
     size_t part_elems = 0;
     double* loss64 = nullptr;
     double* host_loss = nullptr;
-    int use_tc = 1;                  // 256 x 256 inference layers on tcgen05
+    int use_tc = 1;                  // forward pass on the fused tcgen05 kernels
     int sm_count = 0;
     int* tc_error = nullptr;         // device word set by a timed-out tensor-core wait
 };
@@ -443,11 +446,6 @@ static cudaError_t forward_rows(sde_mlp* n, uint64_t Mp, bool store_pre)
     a.C = store_pre ? n->H[0] : nullptr; a.ldc = kH; a.O = n->A[0]; a.ldo = kH; a.bias = n->w + oB1;
     cudaError_t e = gemm<false, false, EPI_FWD_SILU>(a, 0, n->stream);
     for (int l = 1; l < 3 && e == cudaSuccess; ++l) {
-        if (!store_pre && n->use_tc) {
-            e = sde_tc_silu_layer(n->A[l - 1], M, n->wb + (l == 1 ? oW2 : oW3), n->w + (l == 1 ? oB2 : oB3),
-                                  n->A[l], n->tc_error, n->sm_count, n->stream);
-            continue;
-        }
         GemmArgs b{};
         b.M = M; b.N = kH; b.K = kH; b.A = n->A[l - 1]; b.lda = kH;
         b.B = n->wb + (l == 1 ? oW2 : oW3); b.ldb = kH;
@@ -641,6 +639,14 @@ int sde_mlp_forward(sde_mlp* n, const float* x, uint64_t M, float* y)
     for (uint64_t r0 = 0; r0 < M; r0 += chunk) {
         const uint64_t m = (M - r0) < chunk ? (M - r0) : chunk;
         const uint64_t Mp = pad64(m);
+        if (n->use_tc) {
+            // two fused tcgen05 kernels: maps and layers 1-2, layers 3-4 and the output map
+            MLP_CUDA(n, sde_tc_forward((int)m, x + r0 * kIn, n->maps, n->log_mask, n->wb + oW1, n->w + oB1,
+                                       n->wb + oW2, n->w + oB2, n->wb + oW3, n->w + oB3, n->wb + oW4,
+                                       n->w + oB4, n->A[1], y + r0 * kOut, n->tc_error, n->sm_count,
+                                       n->stream));
+            continue;
+        }
         input_map_kernel<<<nblk(Mp * kInPad), 256, 0, n->stream>>>(x + r0 * kIn, m, Mp, n->maps, n->log_mask, n->X);
         MLP_CUDA(n, cudaGetLastError());
         MLP_CUDA(n, forward_rows(n, Mp, false));

@@ -170,9 +170,10 @@ def test_training_fits_a_smooth_function(S):
 
 
 def test_tcgen05_forward_matches_mma_path_and_oracle(S):
-    """The 256 x 256 layers on tcgen05 (FP32 accumulator in tensor memory)
-    against the mma.sync kernels and the FP64 oracle, over a row count that
-    spans two 65536-row chunks and ends in a ragged 128-row tile."""
+    """The fused tcgen05 forward (maps and layers 1-2; layers 3-4 and the
+    output map; FP32 accumulators in tensor memory, two per CTA) against the
+    layer-by-layer mma.sync kernels and the FP64 oracle, over a row count of
+    521 tiles (several per CTA) ending in a ragged 128-row tile."""
     net, p, (shift, scale, mask, osh, osc) = _random_net(S, 9)
     rng = np.random.default_rng(10)
     M = 65536 + 1000 + 37
@@ -197,3 +198,26 @@ def test_tcgen05_forward_matches_mma_path_and_oracle(S):
     yp, _ = omlp.forward(bf16_round(p), xp)
     err = np.abs(y_tc[sel] - (yp * osc + osh)) / osc / np.sqrt(np.mean(yp ** 2, axis=0))
     assert err.max() < 0.03, err.max()
+
+
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 152 * 128 + 5])
+def test_tcgen05_forward_edge_sizes(S, M):
+    """One row, a tile short of full, exactly one tile, one row past it, and
+    one more tile than SMs: the fused path agrees with the mma.sync path."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 12)
+    x = _raw_inputs(np.random.default_rng(M), M)
+    X = torch.from_numpy(x.astype(np.float32)).cuda()
+    try:
+        net.set_tensor_path(1)
+        y_tc = net.forward(X)
+        net.sync()
+        net.set_tensor_path(0)
+        y_mma = net.forward(X)
+        net.sync()
+        y_tc, y_mma = y_tc.cpu().numpy(), y_mma.cpu().numpy()
+    finally:
+        net.close()
+    assert y_tc.shape == (M, 2) and np.isfinite(y_tc).all()
+    d = np.abs(y_tc - y_mma) / osc
+    assert d.max() < 0.02, d.max()
+
