@@ -1,13 +1,15 @@
 """Surrogate-guided parameter scans: label, train, calibrate, screen, select, re-run.
 
 1. Labels: the batched engine (sde_scan, one persistent launch) estimates
-   (<v>, stderr) at N_label random points with N_label_paths paths each.
+   (<v>, stderr) at N_label random points with N_label_paths paths each;
+   half of them are drawn with an edge-dense law (see labels()).
 2. Two networks of the same architecture are trained from different seeds
    on the same labels (sde_mlp_train_step).
-3. Calibration on held-out labelled points: the predicted model error of a
-   point is kappa |v1 - v2| + r0 (the ensemble disagreement and the label
-   noise floor); kappa is the quantile of the held-out residuals that makes
-   the bound cover them.
+3. Calibration on held-out labelled points (split conformal prediction with
+   a normalised score): the predicted model error of a point is
+   kappa (|v1 - v2| + r0), the ensemble disagreement plus the label noise
+   floor r0, and kappa is the 0.999 quantile of the held-out residuals
+   divided by that difficulty.
 4. Screen: both networks predict every grid point (sde_mlp_forward).
 5. Select: sde_guided_flags flags points whose predicted model error exceeds
    tol (0.01, the accuracy asked of the map), whose predicted Monte Carlo
@@ -81,19 +83,22 @@ def predict(nets, X):
     return y1[:, 0].contiguous(), y2[:, 0].contiguous(), (0.5 * (y1[:, 1] + y2[:, 1])).contiguous()
 
 
-def calibrate(nets, Xh, vh, seh, se_scale, coverage=0.99):
-    """kappa and r0 of the predicted-error bound from held-out labels
-    (vh, seh: their Monte Carlo estimates at the label path count)."""
+def calibrate(nets, Xh, vh, seh, se_scale, coverage=0.999):
+    """kappa of the predicted-error bound kappa (|v1 - v2| + r0) from held-out
+    labels (vh, seh: their Monte Carlo estimates at the label path count).
+    The residual is normalised by the difficulty |v1 - v2| + r0 rather than by
+    the disagreement alone, which would make the score blow up where the two
+    networks happen to agree.  Returns r0 as the bound's constant term kappa r0,
+    the form sde_guided_flags takes."""
     v1, v2, lse = predict(nets, Xh)
     v1, v2 = v1.double().cpu().numpy(), v2.double().cpu().numpy()
     vm = 0.5 * (v1 + v2)
     res = np.abs(vm - vh)
-    r0 = 2.0 * float(np.median(seh))                       # label noise floor
+    floor = 2.0 * float(np.median(seh))                    # label noise floor
     d = np.abs(v1 - v2)
-    need = np.maximum(res - r0 - 2.0 * seh, 0.0) / np.maximum(d, 1e-7)
-    kappa = float(np.quantile(need, coverage))
-    covered = float(np.mean(res <= kappa * d + r0 + 2.0 * seh))
-    return {"kappa": kappa, "r0": r0, "se_scale": se_scale, "coverage": covered,
+    kappa = float(np.quantile(res / (d + floor), coverage))
+    covered = float(np.mean(res <= kappa * (d + floor)))
+    return {"kappa": kappa, "r0": kappa * floor, "floor": floor, "se_scale": se_scale, "coverage": covered,
             "rmse": float(np.sqrt(np.mean(res ** 2))), "max_res": float(res.max())}
 
 
@@ -144,11 +149,21 @@ class DichotGuidedScan:
         return dichot_grid_point(self.Fs[i // self.ny], self.bs[i % self.ny], self.spp,
                                  self.transient, self.periods, paths, i)
 
-    def labels(self, n_label, n_hold, stream=7):
-        """Monte Carlo labels at random points of the box (point ids above the grid's)."""
+    def labels(self, n_label, n_hold, stream=7, edge_fraction=0.5):
+        """Monte Carlo labels at random points of the box (point ids above the grid's).
+        A fraction edge_fraction of the points has each coordinate drawn from the
+        arcsine law (density 1 / (pi sqrt(u (1 - u))) on the unit interval,
+        Chebyshev-node density), which samples the box's edges several times more
+        densely than the interior: a smooth regressor's error concentrates at the
+        edges, where it extrapolates.  The held-out points follow the same law, so
+        the calibration sees the edges as often as the labels do."""
         rng = np.random.Generator(np.random.Philox(key=self.seed, counter=[stream, 0, 0, 0]))
-        F = rng.uniform(-0.3, 0.3, n_label + n_hold)
-        b = rng.uniform(0.0, 2.0, n_label + n_hold)
+        n = n_label + n_hold
+        u = rng.uniform(0.0, 1.0, (n, 2))
+        edge = rng.uniform(0.0, 1.0, n) < edge_fraction
+        u[edge] = 0.5 - 0.5 * np.cos(np.pi * u[edge])          # arcsine law
+        F = -0.3 + 0.6 * u[:, 0]
+        b = 2.0 * u[:, 1]
         base = self.nx * self.ny
         pts = [dichot_grid_point(f, bb, self.spp, self.transient, self.periods, self.label_paths,
                                  base + k) for k, (f, bb) in enumerate(zip(F, b))]
@@ -187,7 +202,7 @@ class DichotGuidedScan:
 
 def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=4096, rerun_paths=8192,
                        spp=200, transient=200, periods=2000, tol=0.01, se_tol=0.005, n_valid=2048,
-                       seed=0, steps=16000, valid_stream=13, coverage=0.99, log=print):
+                       seed=0, steps=16000, valid_stream=13, coverage=0.999, log=print):
     """The surrogate-guided scan against plain Monte Carlo on a random sample of
     the same grid points (see the module docstring)."""
     import torch
@@ -260,7 +275,7 @@ def main():
     ap.add_argument("--transient", type=int, default=200)
     ap.add_argument("--valid", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=16000)
-    ap.add_argument("--coverage", type=float, default=0.99)
+    ap.add_argument("--coverage", type=float, default=0.999)
     a = ap.parse_args()
     torch.cuda.set_device(0)
     r = guided_dichot_scan(nx=a.grid, ny=a.grid, n_label=a.labels, label_paths=a.label_paths,
