@@ -19,9 +19,10 @@
 // (tcgen05.mma kind::f16, M = 128, N = 256, FP32 accumulator in tensor memory)
 // and commits them to an mbarrier.  The accumulator alternates between two
 // 256-column halves of tensor memory, so the MMAs of tile t + 1 run while
-// the 8 warps drain tile t: warp w reads 32 TMEM lanes (32 rows, the lane
-// quarter w mod 4 that it may access) of one half of the columns (w / 4) with
-// tcgen05.ld.  Layer 1 (K = 16) runs in the A tile's producer on the legacy
+// the 16 warps drain tile t: warp w reads 32 TMEM lanes (32 rows, the lane
+// quarter w mod 4 that it may access) of one quarter of the columns (w / 4)
+// with tcgen05.ld.  Sixteen warps (four per scheduler) give the SFU-bound
+// SiLU chains of the producer and the drain enough warps to hide latency.  Layer 1 (K = 16) runs in the A tile's producer on the legacy
 // tensor-core path (mma.sync m16n8k16, one K step); layer 4 is a dot product
 // in the epilogue.  Arithmetic is that of the layer-by-layer path (BF16
 // weights and activations, FP32 accumulation and biases) except for the SiLU,
@@ -46,7 +47,8 @@ constexpr int kBRegion = kN * 128;    // bytes of one K-block of W   (32 KB)
 constexpr int kARegion = kRows * 128; // bytes of one K-block of A   (16 KB)
 constexpr int kBBytes = kKBlocks * kBRegion;   // 128 KB
 constexpr int kABytes = kKBlocks * kARegion;   //  64 KB
-constexpr int kThreads = 256;        // 8 warps: warp w reads TMEM lanes 32 (w % 4) .., column half w / 4
+constexpr int kThreads = 512;        // 16 warps: warp w drains TMEM lanes 32 (w % 4) .., column quarter w / 4
+constexpr int kColGroups = kThreads / 128;   // column groups of the epilogue (4 x 64 columns)
 constexpr int kIn = 7, kOut = 2;
 constexpr int kXStride = 24;          // BF16 per staged input / layer-1 weight row (48 bytes: no ldmatrix conflicts)
 constexpr uint32_t kTmemCols = 512;   // two 256-column accumulators
@@ -61,8 +63,8 @@ constexpr int kOffX = kOffBias + kN * 4;                 // 128 x 24 BF16 inputs
 constexpr int kOffW1 = kOffX + kRows * kXStride * 2;     // 256 x 24 BF16 layer-1 weights
 constexpr int kOffB1 = kOffW1 + kN * kXStride * 2;       // 256 FP32
 constexpr int kOffW4 = kOffB1 + kN * 4;                  // 2 x 256 FP32 layer-4 weights
-constexpr int kOffPart = kOffW4 + kOut * kN * 4;         // 128 x 2 FP32 half-row partial outputs
-constexpr int kOffMaps = kOffPart + kRows * kOut * 4;    // 32 FP32 maps, then b4
+constexpr int kOffPart = kOffW4 + kOut * kN * 4;         // 4 x 128 x 2 FP32 partial outputs per column group
+constexpr int kOffMaps = kOffPart + kColGroups * kRows * kOut * 4;   // 32 FP32 maps, then b4
 constexpr int kSmemBytes = kOffMaps + 64 * 4 + 1024;     // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
@@ -154,12 +156,26 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 
 // Input map and layer 1 of the 128 rows from r0, written as SiLU(x W1^T + b1)
 // in BF16 into the swizzled A tile.  Threads 0..127 map one row each into
-// sX; then warp w computes rows 16 w .. 16 w + 15 of all 256 columns with
-// mma.sync (K = 16: the 7 inputs and zero padding), 64 columns (one K-block
-// of the A tile) at a time.  The accumulator fragment holds rows g, g + 8
+// sX; then warp w computes rows 16 (w mod 8) .. + 15 of 128 columns (w / 8
+// selects the half) with mma.sync (K = 16: the 7 inputs and zero padding),
+// 64 columns (one K-block of the A tile) at a time.  The accumulator fragment holds rows g, g + 8
 // and columns 2 t, 2 t + 1 of each 8-column tile: as a BF16 pair it is one
 // 4-byte store, and the swizzle spreads the warp's 32 stores over all banks.
-__device__ __forceinline__ void layer1_tile(const TcArgs& g, int r0, uint8_t* base, uint32_t tid)
+// Raw inputs of row r0 + tid (threads 0..127), loaded a tile ahead of their
+// use so that the global-load latency overlaps the MMA wait and the epilogue.
+__device__ __forceinline__ void prefetch_inputs(const TcArgs& g, int r0, uint32_t tid, float (&xr)[kIn])
+{
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) xr[c] = 0.0f;
+    const int row = r0 + (int)tid;
+    if (tid < (uint32_t)kRows && row < g.M) {
+#pragma unroll
+        for (int c = 0; c < kIn; ++c) xr[c] = g.x[(size_t)row * kIn + c];
+    }
+}
+
+__device__ __forceinline__ void layer1_tile(const TcArgs& g, int r0, uint8_t* base, uint32_t tid,
+                                            const float (&xr)[kIn])
 {
     __nv_bfloat16* sX = (__nv_bfloat16*)(base + kOffX);
     const float* smaps = (const float*)(base + kOffMaps);
@@ -171,7 +187,7 @@ __device__ __forceinline__ void layer1_tile(const TcArgs& g, int r0, uint8_t* ba
         if (row < g.M) {
 #pragma unroll
             for (int c = 0; c < kIn; ++c) {
-                float r = g.x[(size_t)row * kIn + c];
+                float r = xr[c];
                 if ((g.log_mask >> c) & 1u) r = log10f(r);
                 v[c] = __fmul_rn(r - smaps[c], smaps[kIn + c]);
             }
@@ -183,7 +199,8 @@ __device__ __forceinline__ void layer1_tile(const TcArgs& g, int r0, uint8_t* ba
     }
     __syncthreads();
     const uint32_t warp = tid >> 5, lane = tid & 31u;
-    const uint32_t wrow = warp * 16u;
+    const uint32_t wrow = (warp & 7u) * 16u;          // 16 rows
+    const uint32_t kb0 = (warp >> 3) * 2u;            // and two K-blocks (128 columns) per warp
     uint32_t af[4];
     ldsm_x4(smem_addr(sX + (wrow + (lane & 15u)) * kXStride + (lane >> 4) * 8u), af[0], af[1], af[2], af[3]);
     const __nv_bfloat16* sW1 = (const __nv_bfloat16*)(base + kOffW1);
@@ -191,7 +208,7 @@ __device__ __forceinline__ void layer1_tile(const TcArgs& g, int r0, uint8_t* ba
     uint8_t* sA = base + kOffA;
     const uint32_t gi = lane >> 2, ti = lane & 3u;
 #pragma unroll 1
-    for (uint32_t kb = 0; kb < (uint32_t)kKBlocks; ++kb) {
+    for (uint32_t kb = kb0; kb < kb0 + 2u; ++kb) {
         float acc[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -282,12 +299,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
 
     // Stage the A tile of tile t (all threads) and issue its MMAs into the
     // accumulator half acc (one thread), committed to the mbarrier.
+    float xr[kIn];                                   // kProLayer1: the next tile's raw inputs
     auto produce_and_issue = [&](int t, uint32_t acc) {
         if (PRO == kProLoad) {
             load_tile_async(g.A, g.M, t * kRows, sA_a, tid);
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         } else {
-            layer1_tile(g, t * kRows, base, tid);
+            layer1_tile(g, t * kRows, base, tid, xr);
+            prefetch_inputs(g, (t + (int)gridDim.x) * kRows, tid, xr);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -312,6 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     const int tiles = (g.M + kRows - 1) / kRows;
     int t = blockIdx.x;
     uint32_t phase = 0, it = 0;
+    if (PRO == kProLayer1) prefetch_inputs(g, t * kRows, tid, xr);
     if (t < tiles) produce_and_issue(t, tmem);
     for (; t < tiles; t += gridDim.x, ++it) {
         const bool mine = wait_phase(mbar_a, phase);
@@ -330,14 +350,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
         const int tn = t + (int)gridDim.x;
         if (tn < tiles) produce_and_issue(tn, tmem + 256u * ((it + 1u) & 1u));
         const uint32_t acc = tmem + 256u * (it & 1u);
-        const uint32_t quarter = warp & 3u, half = warp >> 2;
+        const uint32_t quarter = warp & 3u, group = warp >> 2;
         const uint32_t trow = quarter * 32u + lane;             // row within the tile
         const int row = t * kRows + (int)trow;
         const uint32_t taddr = acc + ((quarter * 32u) << 16);
         float p0 = 0.0f, p1 = 0.0f;
         const float* sW4 = (const float*)(base + kOffW4);
 #pragma unroll 1
-        for (uint32_t cb = half * (kN / 2); cb < (half + 1u) * (kN / 2); cb += 32u) {
+        for (uint32_t cb = group * (kN / kColGroups); cb < (group + 1u) * (kN / kColGroups); cb += 32u) {
             uint32_t v[32];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -376,14 +396,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
         }
         if (EPI == kEpiOutput) {
             float* spart = (float*)(base + kOffPart);
-            if (half == 1u) {
-                spart[2 * trow] = p0;
-                spart[2 * trow + 1] = p1;
+            if (group != 0u) {
+                spart[(group * kRows + trow) * 2u] = p0;
+                spart[(group * kRows + trow) * 2u + 1u] = p1;
             }
             __syncthreads();
-            if (half == 0u && row < g.M) {
-                const float y0 = p0 + spart[2 * trow] + smaps[32];
-                const float y1 = p1 + spart[2 * trow + 1] + smaps[33];
+            if (group == 0u && row < g.M) {
+                float y0 = p0, y1 = p1;
+#pragma unroll
+                for (uint32_t q = 1; q < (uint32_t)kColGroups; ++q) {   // fixed order
+                    y0 += spart[(q * kRows + trow) * 2u];
+                    y1 += spart[(q * kRows + trow) * 2u + 1u];
+                }
+                y0 += smaps[32];
+                y1 += smaps[33];
                 g.y[(size_t)row * kOut] = fmaf(y0, smaps[2 * kIn + kOut], smaps[2 * kIn]);
                 g.y[(size_t)row * kOut + 1] = fmaf(y1, smaps[2 * kIn + kOut + 1], smaps[2 * kIn + 1]);
             }
