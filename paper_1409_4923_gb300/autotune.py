@@ -4,7 +4,8 @@ Knobs: threads per block (32 .. 128), the grid (0 = one persistent wave sized
 by the occupancy calculator, or a fixed multiple of the SM count), paths per
 lane (1 or 2, interleaved) and steps per launch (0 = the whole run in one
 launch, or Algorithm 5's `samples` steps per launch with the path states kept
-in device memory between launches).  Results never depend on any of them (each
+in device memory between launches).  `tune` serves single-point runs,
+`tune_scan` the batched scan (block and grid).  Results never depend on any of them (each
 path takes the same operations however it is scheduled; the tests check this
 bit for bit), so the tuner only times: it runs a short probe of the same
 kernel variant (same model and noise switches) for each candidate, keeps the
@@ -133,10 +134,61 @@ def tune(model, params, dt, paths, n_probe_steps=2048, seed=0, stream=None, cach
     return dict(res, seconds=shapes, seconds_steps_per_launch=spl)
 
 
+def scan_key(device_name, model, flags):
+    return "%s|scan|model=%d|flags=%d" % (device_name, model, flags)
+
+
+def tune_scan(model, points, seed=0, n_probe_points=256, probe_steps=4096, stream=None, cache=None,
+              force=False, log=None):
+    """Launch shape of the batched scan: time every (block, grid) candidate on a
+    probe scan of the first n_probe_points points, each cut to probe_steps
+    steps (one persistent launch per candidate), and cache the fastest per
+    (device, model, noise flags).  Paths per lane and steps per launch do not
+    apply to the scan kernel.  Returns dict(block, grid)."""
+    import torch
+    cache = cache or cache_path()
+    dev = torch.cuda.get_device_name(torch.cuda.current_device())
+    flags = points[0]["params"].noise_flags
+    k = scan_key(dev, model, flags)
+    data = _load(cache)
+    if not force and k in data:
+        return {"block": data[k]["block"], "grid": data[k]["grid"]}
+    probe = []
+    for p in points[:n_probe_points]:
+        n_tr = min(p["n_transient"], probe_steps // 4)
+        probe.append(dict(p, n_transient=n_tr, n_avg=max(1, probe_steps - n_tr)))
+    eng = E.Engine(model, points[0]["params"], seed=seed, stream=stream)
+    try:
+        _, sms = eng.occupancy(128)
+        eng.scan(probe)                                  # warm-up (module load, workspace, graph)
+        timings = {}
+        for b, g, ppt in candidates(sms):
+            if ppt != 1:
+                continue
+            eng.set_tuning(b, g)
+            eng.scan(probe)                              # captures this shape's graph
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eng.scan(probe)
+            timings[(b, g)] = time.perf_counter() - t0
+            if log:
+                log("scan block %3d grid %5d: %.3f ms" % (b, g, timings[(b, g)] * 1e3))
+        b, g = choose(timings)
+    finally:
+        eng.close()
+    data = _load(cache)
+    data[k] = {"block": b, "grid": g, "probe_points": len(probe), "probe_steps": probe_steps,
+               "seconds": {"%d,%d" % c: t for c, t in timings.items()}}
+    _store(cache, data)
+    return {"block": b, "grid": g}
+
+
 def apply_tuning(engine, t):
     engine.set_tuning(t["block"], t["grid"])
-    engine.set_paths_per_thread(t["ppt"])
-    engine.set_steps_per_launch(t["steps_per_launch"])
+    if "ppt" in t:
+        engine.set_paths_per_thread(t["ppt"])
+    if "steps_per_launch" in t:
+        engine.set_steps_per_launch(t["steps_per_launch"])
 
 
 def apply(engine, model, params, dt, paths, **kw):

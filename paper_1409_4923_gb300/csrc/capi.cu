@@ -191,7 +191,7 @@ int gauss_kind(const sde_params& p)
 // washboards integrate c = 2 pi x (so the SFU cosine takes c directly), the
 // piecewise-linear model integrates x; noise is scaled into those units.
 int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,
-                      uint64_t n_tr, uint64_t n_avg, uint32_t first_item, PointConsts& P)
+                      uint64_t n_tr, uint64_t n_avg, PointConsts& P)
 {
     std::memset(&P, 0, sizeof(P));
     const bool inertial = model == SDE_INERTIAL_WASHBOARD;
@@ -249,7 +249,6 @@ int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint
     P.n_tr = (uint32_t)n_tr;
     P.n_avg = (uint32_t)n_avg;
     P.n_paths = (uint32_t)paths;
-    P.first_item = first_item;
     P.inv_window = 1.0 / ((double)n_avg * dt);
     // the fold subtracts FP32 multiples of the period constant; the unfolded
     // coordinate therefore advances by that constant per folded period
@@ -270,7 +269,6 @@ LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns)
         k1 += 0xBB67AE85u;
     }
     K.n_items = n_items;
-    K.single_point = 1;
     K.budget_ns = budget_ns;
     return K;
 }
@@ -450,7 +448,7 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
     if (rc) return rc;
     const uint64_t items = (paths + 31ull) / 32ull;
     PointConsts P;
-    rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, 0u, P);
+    rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, P);
     if (rc) return rc;
     const Layout L = layout(1, items, 0);
     if ((rc = ensure_ws(c, L.total))) return rc;
@@ -561,7 +559,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
         for (uint64_t t = 0; t < ni; ++t) items.push_back(make_uint2(i, (uint32_t)(32ull * t)));
         ranges[i] = make_uint2(first, (uint32_t)ni);
         int rc = make_point(c, c->model, pts[i].p, pts[i].dt, pts[i].paths, pts[i].n_transient,
-                            pts[i].n_avg, first, P[i]);
+                            pts[i].n_avg, P[i]);
         if (rc) return rc;
     }
     const bool use_scan_kernel = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
@@ -744,7 +742,7 @@ int sde_begin(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_a
     int rc = validate_run(c, paths, dt, n_tr, n_avg);
     if (rc) return rc;
     PointConsts P;
-    if ((rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, 0u, P))) return rc;
+    if ((rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, P))) return rc;
     SegmentedRun r;
     r.p = c->p;
     r.seed = c->seed;
@@ -771,7 +769,7 @@ int sde_advance(sde_ctx* c, uint64_t n_steps, const sde_path_out* out, uint64_t*
     const uint64_t na = r.n_done;
     const uint64_t nb = (n_steps == 0 || n_steps >= total - na) ? total : na + n_steps;
     PointConsts P;
-    int rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, 0u, P);
+    int rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, P);
     if (rc) return rc;
     const Layout L = layout(1, r.items, 0);
     if ((rc = ensure_ws(c, L.total))) return rc;
@@ -879,7 +877,7 @@ int sde_restore(sde_ctx* c, const void* buf, uint64_t bytes)
     const unsigned char* src = (const unsigned char*)buf + sizeof(CkptHeader);
     if (fnv1a64(src, sb) != h.checksum) return fail(c, SDE_EINVAL, "checkpoint checksum mismatch");
     PointConsts P;
-    if ((rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, 0u, P))) return rc;
+    if ((rc = make_point(c, c->model, r.p, r.dt, r.paths, r.n_tr, r.n_avg, P))) return rc;
     if (sb) {
         // event counters: planes 0 (eP), 1 (JP), 4 (eD), 5 (JD), 6 (dst) of the u32 block
         const bool pois = (r.p.noise_flags & SDE_NOISE_POISSON) != 0;

@@ -22,5 +22,5 @@ int dich_kind(uint32_t flags);
 
 // FP32/FP64 kernel constants of one point and of one launch.
 int make_point(sde_ctx* c, sde_model model, const sde_params& p, double dt, uint64_t paths,
-               uint64_t n_tr, uint64_t n_avg, uint32_t first_item, sde::PointConsts& P);
+               uint64_t n_tr, uint64_t n_avg, sde::PointConsts& P);
 sde::LaunchConsts make_launch(uint64_t seed, uint32_t n_items, uint64_t budget_ns);

@@ -27,7 +27,6 @@ enum : int32_t { kStatusOk = 0, kStatusTimedOut = -4 };
 struct LaunchConsts {
     uint32_t rk0[10], rk1[10];   // Philox round keys: seed + r * Weyl constant
     uint32_t n_items;            // warp items in the launch
-    uint32_t single_point;       // 1: one point, item i covers paths 32 i .. 32 i + 31
     uint64_t budget_ns;          // device-time budget per warp (from its start), 0 = none
 };
 
@@ -49,13 +48,12 @@ struct PointConsts {
     float mua_cl2, mub_cl2;     // ln 2 / (mu dt)
     double inv_lambda, inv_mua, inv_mub, dt64;   // exact (FP64) waiting times
     uint32_t d0_thresh;         // initial state F_b iff (w >> 8) < d0_thresh
-    uint32_t gauss_pad;
     // initial state
     float x0_lo, x0_span, v0_lo, v0_span;
     // counters
     uint32_t c1_init, c1_gauss, c1_pois, c1_dich;   // (tag << 30) | point
     // run
-    uint32_t n_tr, n_avg, n_paths, first_item;
+    uint32_t n_tr, n_avg, n_paths;
     double inv_window;  // 1 / (n_avg dt)
     double period;      // spatial period L in x units
     double coord_to_x;  // x = coordinate * coord_to_x (1 / 2 pi for washboards)

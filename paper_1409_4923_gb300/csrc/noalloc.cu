@@ -80,7 +80,7 @@ extern "C" int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t se
     if (e != cudaSuccess)
         return fail(nullptr, SDE_ECUDA, std::string("sde_run_noalloc set-up: ") + cudaGetErrorString(e));
     PointConsts P;
-    if ((rc = make_point(nullptr, model, *p, dt, paths, n_transient, n_avg, 0u, P))) return rc;
+    if ((rc = make_point(nullptr, model, *p, dt, paths, n_transient, n_avg, P))) return rc;
     const uint32_t items = (uint32_t)((paths + 31ull) / 32ull);
     const LaunchConsts K = make_launch(seed, items, 0);
     char* b = (char*)base;

@@ -139,6 +139,13 @@ class DichotGuidedScan:
         self.eng = E.Engine(0, E.make_params(**W.dichot_point()), seed=seed)
         self.torch = torch
         self.nets = None
+        # launch shape of the scans from the autotuner (a probe on the grid's points)
+        from . import autotune
+        probe = []
+        for i in range(0, nx * ny, max(1, (nx * ny) // 256)):
+            pt = self.grid_point(i, rerun_paths)
+            probe.append(dict(pt, params=E.make_params(**pt["params"])))
+        autotune.apply_tuning(self.eng, autotune.tune_scan(0, probe, seed=seed))
 
     def close(self):
         self.eng.close()

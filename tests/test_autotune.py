@@ -60,3 +60,26 @@ def test_tune_on_gpu(tmp_path):
         sums.append(eng.stats()["sums"])
         eng.close()
     assert sums[0] == sums[1]
+
+
+@pytest.mark.gpu
+def test_tune_scan_on_gpu(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import engine as E, workloads as W
+    pts = [dict(p, params=E.make_params(**p["params"])) for p in W.scan_64x64()[:64]]
+    cache = str(tmp_path / "tune.json")
+    t = AT.tune_scan(0, pts, n_probe_points=32, probe_steps=1024, cache=cache)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert t["block"] in AT.BLOCKS and t["grid"] % sms == 0
+    assert AT.tune_scan(0, pts, cache=cache) == t
+    sums = []
+    for knobs in (AT.DEFAULT, t):
+        eng = E.Engine(0, pts[0]["params"], seed=2)
+        AT.apply_tuning(eng, knobs)
+        short = [dict(p, n_avg=500, n_transient=50) for p in pts[:16]]
+        sums.append([r["sums"] for r in eng.scan(short)])
+        eng.close()
+    assert sums[0] == sums[1]
+
