@@ -54,7 +54,8 @@ int sde_mlp_set_params(sde_mlp* net, const float* host_params);
 int sde_mlp_get_params(sde_mlp* net, float* host_params);
 
 /* Forward pass: x (device, M x 7 FP32 raw inputs) -> y (device, M x 2 FP32).
- * Any M >= 1; large M runs in chunks of 65536 rows.  Asynchronous. */
+ * Any M >= 1; large M runs in chunks (2^20 rows on the tcgen05 path, 65536
+ * on the mma.sync path).  Asynchronous. */
 int sde_mlp_forward(sde_mlp* net, const float* x, uint64_t M, float* y);
 
 /* Gradients of the mean squared error of the standardised outputs,
@@ -70,11 +71,13 @@ int sde_mlp_gradients(sde_mlp* net, const float* x, const float* t, uint64_t M,
 int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M, float lr,
                        float beta1, float beta2, float eps, float* loss_dev);
 
-/* Matrix path of the forward pass's two 256 x 256 layers: 1 (default) the
- * fifth-generation tensor cores (tcgen05.mma with the FP32 accumulator in
- * tensor memory, persistent CTAs holding the layer's weights in shared
- * memory), 0 the warp-level mma.sync kernels that also serve training.
- * Results agree to FP32 accumulation order. */
+/* Matrix path of the forward pass: 1 (default) two fused kernels on the
+ * fifth-generation tensor cores (input map and layers 1-2; layers 3-4 and
+ * the output map; tcgen05.mma with FP32 accumulators in tensor memory,
+ * persistent CTAs holding a 256 x 256 layer's weights in shared memory, SiLU
+ * through tanh), 0 the layer-by-layer warp-level mma.sync kernels that also
+ * serve training.  Results agree within the BF16 rounding of the
+ * activations. */
 int sde_mlp_set_tensor_path(sde_mlp* net, int use_tcgen05);
 
 /* Wait for the network's stream and report device-side failures: SDE_ETIMEDOUT
