@@ -48,6 +48,8 @@ def lib():
         path = _build.build()
         L = ctypes.CDLL(path)
         L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+        L.orc_philox_many.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.c_void_p]
         L.orc_run_paths.argtypes = [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
@@ -88,6 +90,15 @@ def philox4x32_10(ctr, key):
     o = (ctypes.c_uint32 * 4)()
     lib().orc_philox4x32_10(c, k, o)
     return [int(x) for x in o]
+
+
+def philox_many(ctr, key):
+    """Philox4x32-10 of an (n, 4) uint32 array of counters under one key -> (n, 4) words."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32)
+    out = np.zeros_like(ctr)
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xffffffff for x in key])
+    lib().orc_philox_many(ctr.ctypes.data, ctr.shape[0], k, out.ctypes.data)
+    return out
 
 
 def stream_words(seed, tag, point, path, idx):

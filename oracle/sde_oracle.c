@@ -40,6 +40,12 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+/* The same generator over n counters ctr[4 i .. 4 i + 3] (for bulk tests). */
+void orc_philox_many(const uint32_t* ctr, uint64_t n, const uint32_t key[2], uint32_t* out)
+{
+    for (uint64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 enum { TAG_INIT = 0, TAG_GAUSS = 1, TAG_POIS = 2, TAG_DICH = 3 };
 
 void orc_stream_words(uint64_t seed, uint32_t tag, uint32_t point, uint32_t path,

@@ -89,6 +89,7 @@ typedef struct {
 } orc_path_out;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_philox_many(const uint32_t* ctr, uint64_t n, const uint32_t key[2], uint32_t* out);
 
 /* Integrate paths path0 .. path0+npaths-1 for n_transient + n_avg steps of dt.
  * nthreads <= 0 uses one thread.  Returns 0, or -1 on invalid arguments. */

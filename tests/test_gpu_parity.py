@@ -52,6 +52,25 @@ def test_philox_bitexact(E, orc):
         eng.close()
 
 
+def test_philox_bitexact_million(E, orc):
+    """10^6 (key, counter) pairs: random counters, the all-zero and all-one
+    counters, and the stream contract's tag and index-carry edges."""
+    rng = np.random.default_rng(21)
+    ctr = rng.integers(0, 2 ** 32, size=(500000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xffffffff
+    ctr[2:6, 1] = np.array([0, 1, 2, 3], dtype=np.uint32) << 30        # the four tags, point 0
+    ctr[6:10, 0] = 0xffffffff                                         # index low word at its top
+    eng = E.Engine(0, E.make_params(gamma=1.0), seed=0)
+    try:
+        for seed in (0x0123456789ABCDEF, 2 ** 64 - 1):
+            got = eng.philox_words(ctr, seed)
+            want = orc.philox_many(ctr, [seed & 0xffffffff, seed >> 32])
+            assert np.array_equal(got, want), seed
+    finally:
+        eng.close()
+
+
 def _cases(W):
     pois = W.poisson_point()
     dich = W.dichot_point()
@@ -100,6 +119,28 @@ def test_per_path_short_horizon(E, W, orc, case, n_tr, n_avg):
     assert g_st["n"] == paths
     # the device FP64 sums equal the sums of the device per-path values
     assert abs(g_st["sums"][1] - math.fsum(g["vbar"])) <= 1e-12 * (1 + np.abs(g["vbar"]).sum())
+
+
+@pytest.mark.parametrize("case,n", [("inertial-poisson", 100), ("inertial-dichot", 200),
+                                    ("inertial-all-noises", 100), ("overdamped-washboard", 800)])
+def test_per_path_one_drive_period(E, W, orc, case, n):
+    """Per path over one drive period (spp steps; 800 steps of the overdamped
+    washboard, which is not chaotic): |dX| <= 1e-4 and |dv| <= 1e-3.  The
+    driven inertial washboard is chaotic: FP32 rounding grows by about e^{8}
+    over a period (measured maxima 5.7e-5 in X and 3.0e-4 in v over 1000
+    paths) and reaches O(1) by eight periods, where only the ensemble
+    averages can be compared."""
+    model, prm, dt = _cases(W)[case]
+    paths = 1000
+    _, g = gc.engine_run(E, torch, model, prm, 11, paths, dt, 0, n)
+    r = orc.run_paths(model, gc.oracle_params(orc, prm), 11, 0, paths, dt, 0, n)
+    ok, n_excl = gc.events_equal(g, r)
+    assert ok and n_excl == 0
+    dX = np.abs(g["X_f"] - r["X_f"])
+    assert dX.max() <= 1e-4, (case, np.quantile(dX, [0.5, 0.99, 1.0]))
+    if model == 0:
+        dv = np.abs(g["v_f"].astype(np.float64) - r["v_f"])
+        assert dv.max() <= 1e-3, (case, np.quantile(dv, [0.5, 0.99, 1.0]))
 
 
 @pytest.mark.parametrize("case", ["inertial-poisson", "inertial-dichot", "pwl-model-I-II"])

@@ -46,3 +46,13 @@ def test_philox_words_uniform(orc):
     exp = len(top) / 256.0
     chi2 = ((counts - exp) ** 2 / exp).sum()
     assert 180 < chi2 < 340     # 255 dof: mean 255, sd ~22.6
+
+
+def test_batched_call_is_the_same_generator(orc):
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2 ** 32, size=(500, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0x89ABCDEF, 0x01234567]
+    got = orc.philox_many(ctr, key)
+    for i in range(0, 500, 7):
+        assert list(got[i]) == orc.philox4x32_10(list(ctr[i]), key)
+
