@@ -32,7 +32,7 @@ UNIT = "path-steps/s"
 
 # Algorithmic lane operations per path-step of the inertial model with
 # three-point Gaussian and one jump noise (the method's own arithmetic, counted
-# from Algorithms 1-4 and the Philox definition; derivation in the design doc):
+# from Algorithms 1-4 and the Philox definition):
 #   Algorithm 1 on (x, v): 3 drift evaluations x (cos argument 1, SFU cos 1,
 #   force FMA 1, damping FMA 1) = 12, state updates and trapezoid sums 10,
 #   fold of x (scale, round, subtract, count) 4, window sums of v, v^2 2 -> 28
@@ -254,7 +254,9 @@ def run_engine(args):
         "e2e": {"value": units * world / e2e_t, "unit": UNIT,
                 "h2d_bytes_per_step": E.ctypes.sizeof(E.Params) + 8,
                 "d2h_bytes_per_step": 5 * 8 + 4},
-        "gpu_launches": 2 * args.steps,
+        # per step: the path kernel (one launch per steps_per_launch segment) and the fold
+        "gpu_launches": args.steps * (1 + (-(-steps_per_path // knobs["steps_per_launch"])
+                                           if knobs["steps_per_launch"] else 1)),
         "clocks": clocks,
         "result": {"mean_v": st["mean_v"], "stderr_v": st["stderr_v"], "tmean_v": st["tmean_v"],
                    "tvar_v": st["tvar_v"]},

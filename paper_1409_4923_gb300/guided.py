@@ -19,7 +19,7 @@
    paths under the grid point's own random counter, so a re-run value equals
    the plain Monte Carlo map's value at that point bit for bit.
 
-The plain Monte Carlo method stays both judge and fallback.  Orchestration
+The plain Monte Carlo method stays both the arbiter and the fallback.  Orchestration
 only: every arithmetic step runs in libsde.so's kernels.
 """
 import ctypes
