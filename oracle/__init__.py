@@ -50,6 +50,10 @@ def lib():
         L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
         L.orc_philox_many.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.c_void_p]
+        L.orc_local_error.argtypes = [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                      ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.orc_local_error.restype = ctypes.c_int
         L.orc_run_paths.argtypes = [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
@@ -99,6 +103,20 @@ def philox_many(ctr, key):
     k = (ctypes.c_uint32 * 2)(*[int(x) & 0xffffffff for x in key])
     lib().orc_philox_many(ctr.ctypes.data, ctr.shape[0], k, out.ctypes.data)
     return out
+
+
+def local_error(model, params: Params, seed, path0, npaths, dt, n_steps, nthreads=None):
+    """Sec. 4's chi over npaths paths x n_steps steps: dict of rms and max of
+    chi_x (x units) and chi_v (inertial model)."""
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    o = (ctypes.c_double * 4)()
+    rc = lib().orc_local_error(model, ctypes.byref(params), seed, path0, npaths, dt, n_steps,
+                               nthreads, o)
+    if rc != 0:
+        raise ValueError("orc_local_error rejected its arguments")
+    n = float(npaths) * float(n_steps)
+    return {"rms_x": (o[0] / n) ** 0.5, "rms_v": (o[1] / n) ** 0.5, "max_x": o[2], "max_v": o[3]}
 
 
 def stream_words(seed, tag, point, path, idx):

@@ -229,8 +229,12 @@ static void ctx_setup(orc_ctx* c, int model, const orc_params* p, uint64_t seed,
     c->kink_min = 1.0;
 }
 
+/* chi (may be NULL) accumulates Sec. 4's local-error indicator chi =
+ * (predictor) - (corrector) of each step, without the jump increments (which
+ * are exact, not discretisation error): chi[0] += chi_x^2, chi[1] += chi_v^2,
+ * chi[2] = max |chi_x|, chi[3] = max |chi_v| (v: inertial model only). */
 static void run_one(int model, const orc_params* p, uint64_t seed, uint32_t path,
-                    double dt, uint64_t n_tr, uint64_t n_avg, orc_path_out* o)
+                    double dt, uint64_t n_tr, uint64_t n_avg, orc_path_out* o, double* chi)
 {
     orc_ctx c;
     ctx_setup(&c, model, p, seed, path, dt);
@@ -272,10 +276,18 @@ static void run_one(int model, const orc_params* p, uint64_t seed, uint32_t path
             double F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             xb = x + 0.5 * (F1x + F2x) * dt;                      /* predictor */
             vb = v + 0.5 * (F1v + F2v) * dt + dxi;
+            const double xp = xb, vp = vb;
             F2x = vb;
             F2v = -p->gamma * vb + minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             x = x + 0.5 * (F1x + F2x) * dt;                       /* corrector */
             v = v + 0.5 * (F1v + F2v) * dt + dxi + deta + dgam;
+            if (chi) {
+                const double cx = xp - x, cv = vp - (v - deta - dgam);
+                chi[0] += cx * cx;
+                chi[1] += cv * cv;
+                if (fabs(cx) > chi[2]) chi[2] = fabs(cx);
+                if (fabs(cv) > chi[3]) chi[3] = fabs(cv);
+            }
         } else {
             double F1 = minus_dV(&c, x) + drive(&c, t0) + gdrift;
             double xb = x + F1 * dt + dxi;
@@ -283,6 +295,11 @@ static void run_one(int model, const orc_params* p, uint64_t seed, uint32_t path
             xb = x + 0.5 * (F1 + F2) * dt + dxi;                  /* predictor */
             F2 = minus_dV(&c, xb) + drive(&c, t1) + gdrift;
             x = x + 0.5 * (F1 + F2) * dt + dxi + deta + dgam;     /* corrector */
+            if (chi) {
+                const double cx = xb - (x - deta - dgam);
+                chi[0] += cx * cx;
+                if (fabs(cx) > chi[2]) chi[2] = fabs(cx);
+            }
         }
         if (n + 1 == n_tr) X_i = x;
         if (n + 1 > n_tr && inertial) {
@@ -310,7 +327,7 @@ static void run_one(int model, const orc_params* p, uint64_t seed, uint32_t path
 
 typedef struct {
     int model; const orc_params* p; uint64_t seed; uint64_t first, count;
-    double dt; uint64_t n_tr, n_avg; orc_path_out* out;
+    double dt; uint64_t n_tr, n_avg; orc_path_out* out; double* chi;
 } orc_job;
 
 static void* orc_worker(void* arg)
@@ -318,13 +335,47 @@ static void* orc_worker(void* arg)
     orc_job* jb = (orc_job*)arg;
     for (uint64_t i = 0; i < jb->count; ++i)
         run_one(jb->model, jb->p, jb->seed, (uint32_t)(jb->first + i), jb->dt,
-                jb->n_tr, jb->n_avg, jb->out + i);
+                jb->n_tr, jb->n_avg, jb->out + i, jb->chi ? jb->chi + 4 * i : NULL);
     return NULL;
 }
+
+static int run_paths_impl(int model, const orc_params* p, uint64_t seed, uint64_t path0,
+                          uint64_t npaths, double dt, uint64_t n_tr, uint64_t n_avg,
+                          int nthreads, orc_path_out* out, double* chi);
 
 int orc_run_paths(int model, const orc_params* p, uint64_t seed, uint64_t path0,
                   uint64_t npaths, double dt, uint64_t n_tr, uint64_t n_avg,
                   int nthreads, orc_path_out* out)
+{
+    return run_paths_impl(model, p, seed, path0, npaths, dt, n_tr, n_avg, nthreads, out, NULL);
+}
+
+int orc_local_error(int model, const orc_params* p, uint64_t seed, uint64_t path0,
+                    uint64_t npaths, double dt, uint64_t n_steps, int nthreads, double out4[4])
+{
+    if (!out4) return -1;
+    out4[0] = out4[1] = out4[2] = out4[3] = 0.0;
+    if (npaths == 0) return 0;
+    orc_path_out* po = (orc_path_out*)calloc((size_t)npaths, sizeof(orc_path_out));
+    double* chi = (double*)calloc((size_t)npaths * 4, sizeof(double));
+    if (!po || !chi) { free(po); free(chi); return -1; }
+    int rc = run_paths_impl(model, p, seed, path0, npaths, dt, 0, n_steps, nthreads, po, chi);
+    if (rc == 0) {
+        for (uint64_t i = 0; i < npaths; ++i) {       /* fixed order */
+            out4[0] += chi[4 * i];
+            out4[1] += chi[4 * i + 1];
+            if (chi[4 * i + 2] > out4[2]) out4[2] = chi[4 * i + 2];
+            if (chi[4 * i + 3] > out4[3]) out4[3] = chi[4 * i + 3];
+        }
+    }
+    free(po);
+    free(chi);
+    return rc;
+}
+
+static int run_paths_impl(int model, const orc_params* p, uint64_t seed, uint64_t path0,
+                          uint64_t npaths, double dt, uint64_t n_tr, uint64_t n_avg,
+                          int nthreads, orc_path_out* out, double* chi)
 {
     if (!p || !out || !(dt > 0.0) || model < 0 || model > ORC_OVERDAMPED_LINEAR) return -1;
     if (path0 + npaths > 0x100000000ull || p->point >= (1u << 30)) return -1;
@@ -337,7 +388,7 @@ int orc_run_paths(int model, const orc_params* p, uint64_t seed, uint64_t path0,
     uint64_t per = npaths / (uint64_t)nthreads, extra = npaths % (uint64_t)nthreads, at = 0;
     for (int t = 0; t < nthreads; ++t) {
         uint64_t cnt = per + ((uint64_t)t < extra ? 1 : 0);
-        orc_job jb = { model, p, seed, path0 + at, cnt, dt, n_tr, n_avg, out + at };
+        orc_job jb = { model, p, seed, path0 + at, cnt, dt, n_tr, n_avg, out + at, chi ? chi + 4 * at : NULL };
         jobs[t] = jb;
         at += cnt;
     }

@@ -97,6 +97,14 @@ int orc_run_paths(int model, const orc_params* p, uint64_t seed, uint64_t path0,
                   uint64_t npaths, double dt, uint64_t n_transient, uint64_t n_avg,
                   int nthreads, orc_path_out* out);
 
+/* Sec. 4's local-error indicator chi = (predictor) - (corrector) of every
+ * step, without the jump increments, over n_steps steps of paths path0 ..
+ * path0 + npaths - 1 from their initial states: out4 = {sum chi_x^2,
+ * sum chi_v^2, max |chi_x|, max |chi_v|} over all paths and steps (x in x
+ * units; v components zero for the overdamped models).  Returns 0 or -1. */
+int orc_local_error(int model, const orc_params* p, uint64_t seed, uint64_t path0,
+                    uint64_t npaths, double dt, uint64_t n_steps, int nthreads, double out4[4]);
+
 /* Ensemble statistics of Eq. 31 over n path records:
  * res = {n, mean vbar, sample variance of vbar, stderr, time mean of v,
  *        time variance of v, sum vbar, sum vbar^2}. */

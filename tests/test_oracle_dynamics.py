@@ -165,6 +165,44 @@ def test_dichotomous_force_as_drift_is_second_order(orc, model):
         assert all(lo < q < hi for q in rates), (flags, errs)
 
 
+def test_local_error_chi_closed_form(orc):
+    """Sec. 4's chi = predictor - corrector.  For x' = -k x, Algorithm 1 gives
+    Euler x(1 - h), predictor x(1 - h + h^2/2), corrector
+    x(1 - h + h^2/2 - h^3/4) with h = k dt, so chi_n = x_n h^3 / 4 exactly, on
+    x_n = x0 alpha^n with alpha the corrector's factor."""
+    k, x0, n = 0.9, 1.0, 40
+    for dt in (0.1, 0.05, 0.025):
+        h = k * dt
+        alpha = 1.0 - h + h * h / 2.0 - h ** 3 / 4.0
+        chi = x0 * alpha ** np.arange(n) * h ** 3 / 4.0
+        r = orc.local_error(orc.OVERDAMPED_LINEAR, orc.make_params(V0=k, x0_lo=x0, x0_hi=x0), 0, 0, 4, dt, n)
+        assert abs(r["rms_x"] / math.sqrt(np.mean(chi ** 2)) - 1.0) < 1e-9
+        assert abs(r["max_x"] / chi[0] - 1.0) < 1e-9
+        assert r["rms_v"] == 0.0
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_local_error_scales_as_dt_cubed(orc, model):
+    """Noise-free washboards: chi is the local error of a second-order scheme,
+    O(dt^3): halving dt divides it by about 8 (inertial: both components)."""
+    kw = (dict(gamma=0.9, a=4.2, omega=4.9, F=0.1, v0_lo=-2.0, v0_hi=2.0) if model == 0 else
+          dict(V0=0.2, a=0.5, omega=4.9, F=0.1))
+    rs = [orc.local_error(model, orc.make_params(x0_hi=1.0, **kw), 0, 0, 64, dt, int(round(1.0 / dt)))
+          for dt in (0.02, 0.01, 0.005)]
+    for key in (("rms_x", "rms_v") if model == 0 else ("rms_x",)):
+        for a, b in zip(rs[:-1], rs[1:]):
+            assert 7.0 < a[key] / b[key] < 9.0, (key, a[key] / b[key])
+
+
+def test_local_error_excludes_jumps(orc):
+    """The jump increments are exact and enter only the corrector: a force-free
+    overdamped particle under Poisson and dichotomous noise has chi = 0."""
+    p = orc.make_params(V0=0.0, zeta=0.3, Fa=0.5, Fb=0.5, mua=2.0, mub=2.0, noise=orc.POISSON | orc.DICHOT,
+                        **{"lambda": 3.0})
+    r = orc.local_error(orc.OVERDAMPED_WASHBOARD, p, 0, 0, 16, 0.01, 500)
+    assert r["max_x"] < 1e-15
+
+
 @pytest.mark.parametrize("compensated", [False, True])
 def test_poisson_free_particle(orc, compensated):
     """Overdamped, no force, Poisson only: x_n - x_0 is a sum of n i.i.d. increments
