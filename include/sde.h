@@ -224,6 +224,18 @@ int sde_checkpoint(sde_ctx* ctx, void* buf, uint64_t bytes);
  * Synchronises the stream. */
 int sde_restore(sde_ctx* ctx, const void* buf, uint64_t bytes);
 
+/* Local-error indicator of Sec. 4: chi = (predictor) - (corrector) of each
+ * step, without the jump increments (exact, not discretisation error), over
+ * n_steps steps of `paths` paths from their initial states with the
+ * context's parameters and seed.  Writes out4 (host) = {rms chi_x (x units),
+ * rms chi_v, max |chi_x|, max |chi_v|} over all paths and steps (the v
+ * entries are 0 for the overdamped models).  chi is the local error of the
+ * second-order scheme: O(dt^3) without noise, O(dt^2.5) with Gaussian noise,
+ * so a step size can be chosen per run from two probes (the paper suggests
+ * chi for step-size control; the steps of one run stay uniform, as the
+ * event streams require).  Synchronises the stream.  EINVAL as sde_run. */
+int sde_local_error(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_steps, double* out4);
+
 /* Reduce `n` device doubles `vals` to {n, sum, sum of squares} with the same
  * FP64 fold the engine uses (pairwise within a warp, Kahan across items).
  * `out3` is a host array of three doubles.  Synchronises the stream. */

@@ -17,6 +17,23 @@ cudaError_t launch_segment_m##M(bool, int, int, const PointConsts&, const Launch
                                 const PathOutPtrs&, int, int, int, cudaStream_t);
 SDE_SEG_DECL(0) SDE_SEG_DECL(1) SDE_SEG_DECL(2)
 #undef SDE_SEG_DECL
+#define SDE_CHI_DECL(M) \
+cudaError_t launch_chi_m##M(bool, int, int, const PointConsts&, const LaunchConsts&, uint32_t, \
+                            const Workspace&, int, int, int, cudaStream_t);
+SDE_CHI_DECL(0) SDE_CHI_DECL(1) SDE_CHI_DECL(2)
+#undef SDE_CHI_DECL
+
+cudaError_t launch_chi(int model, bool pois, int dich, int gauss, const PointConsts& P,
+                       const LaunchConsts& K, uint32_t n_steps, const Workspace& ws, int bt, int gb, int sm,
+                       cudaStream_t st)
+{
+    switch (model) {
+    case kModelInertial: return launch_chi_m0(pois, dich, gauss, P, K, n_steps, ws, bt, gb, sm, st);
+    case kModelOverdampedWashboard: return launch_chi_m1(pois, dich, gauss, P, K, n_steps, ws, bt, gb, sm, st);
+    case kModelPWL: return launch_chi_m2(pois, dich, gauss, P, K, n_steps, ws, bt, gb, sm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_point(int model, bool pois, int dich, int gauss, int ppt, const PointConsts& P,
                          const LaunchConsts& K, const Workspace& ws, const PathOutPtrs& po,

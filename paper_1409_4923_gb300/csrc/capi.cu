@@ -906,6 +906,42 @@ int sde_restore(sde_ctx* c, const void* buf, uint64_t bytes)
     return SDE_OK;
 }
 
+int sde_local_error(sde_ctx* c, uint64_t paths, double dt, uint64_t n_steps, double* out4)
+{
+    if (!c || !out4) return SDE_EINVAL;
+    int rc = validate_run(c, paths, dt, 0, n_steps);
+    if (rc) return rc;
+    PointConsts P;
+    if ((rc = make_point(c, c->model, c->p, dt, paths, 0, n_steps, P))) return rc;
+    const uint64_t items = (paths + 31ull) / 32ull;
+    const Layout L = layout(1, items, 0);
+    if ((rc = ensure_ws(c, L.total))) return rc;
+    if ((rc = ensure_host(c, 5 * sizeof(double) * items + 64))) return rc;
+    ++c->ws_gen;
+    char* base = (char*)c->ws;
+    Workspace ws{(uint32_t*)base, (int32_t*)(base + 4), (double*)(base + L.off_partials)};
+    SDE_CUDA(c, cudaMemsetAsync(base, 0, 8, c->stream));
+    const LaunchConsts K = make_launch(c->seed, (uint32_t)items, 0);
+    const uint32_t f = c->p.noise_flags;
+    SDE_CUDA(c, launch_chi((int)c->model, (f & SDE_NOISE_POISSON) != 0, dich_kind(f), gauss_kind(c->p), P, K,
+                           (uint32_t)n_steps, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+    SDE_CUDA(c, cudaMemcpyAsync(c->host, ws.partials, 5 * sizeof(double) * items, cudaMemcpyDeviceToHost,
+                                c->stream));
+    SDE_CUDA(c, cudaStreamSynchronize(c->stream));
+    double n = 0.0, sx = 0.0, sv = 0.0, mx = 0.0, mv = 0.0;
+    for (uint64_t i = 0; i < items; ++i) {                  // fixed order
+        const double* o = c->host + 5 * i;
+        n += o[0]; sx += o[1]; sv += o[2];
+        mx = std::max(mx, o[3]); mv = std::max(mv, o[4]);
+    }
+    const double cnt = n * (double)n_steps;
+    out4[0] = std::sqrt(sx / cnt) * P.coord_to_x;
+    out4[1] = std::sqrt(sv / cnt);
+    out4[2] = mx * P.coord_to_x;
+    out4[3] = mv;
+    return SDE_OK;
+}
+
 int sde_reduce_f64(sde_ctx* c, const double* vals, uint64_t n, double* out3)
 {
     if (!c || (!vals && n) || !out3) return SDE_EINVAL;

@@ -1,0 +1,12 @@
+// chi_m1.cu -- instantiations of the local-error diagnostic kernel for model 1.
+#include "chi_kernels.cuh"
+
+namespace sde {
+
+cudaError_t launch_chi_m1(bool pois, int dich, int gauss, const PointConsts& P, const LaunchConsts& K,
+                          uint32_t n_steps, const Workspace& ws, int bt, int gb, int sm, cudaStream_t st)
+{
+    return launch_chi_model<1>(pois, dich, gauss, P, K, n_steps, ws, bt, gb, sm, st);
+}
+
+}  // namespace sde

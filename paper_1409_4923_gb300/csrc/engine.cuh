@@ -218,9 +218,13 @@ __device__ __forceinline__ float with_jumps(float h1, float pj, float dg)
 // t_n, t_{n+1}.  The jump increments enter the corrector only (Algorithm 1);
 // with DICH == 2 the dichotomous force is instead a drift term, constant over
 // the step, in all three drift evaluations.
-template <int MODEL, bool POIS, int DICH, bool ACC, bool FOLD>
+// With CHI, chi receives Sec. 4's local-error indicator of the step, the
+// predictor minus the corrector without the jump increments: chi[0] in the
+// coordinate (whdt (v_Euler - v_predictor) = whdt (b1 - b2) / 2 inertial,
+// (b2 - b3) / 2 overdamped), chi[1] in v ((b2 - b3) / 2, inertial).
+template <int MODEL, bool POIS, int DICH, bool ACC, bool FOLD, bool CHI = false>
 __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, float dxi, float pj,
-                                        float dg, float d0, float d1)
+                                        float dg, float d0, float d1, float* chi = nullptr)
 {
     if (DICH == 2) {
         d0 += dg;
@@ -240,6 +244,10 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         S.c = fmaf(P.whdt, vb, ch);                                         // corrector x
         S.v = fmaf(0.5f, b3, with_jumps<POIS, DICH>(h1, pj, dg));           // corrector v
         accumulate<ACC>(S);
+        if (CHI) {
+            chi[0] = __fmul_rn(P.whdt, __fmul_rn(0.5f, b1 - b2));
+            chi[1] = __fmul_rn(0.5f, b2 - b3);
+        }
     } else {
         const float b1 = add_force_dt<MODEL>(d0, S.c, P);
         const float cxi = S.c + dxi;
@@ -249,6 +257,10 @@ __device__ __forceinline__ void pc_step(PathState& S, const PointConsts& P, floa
         cb = fmaf(0.5f, b2, h1);                                            // predictor
         const float b3 = add_force_dt<MODEL>(d1, cb, P);
         S.c = fmaf(0.5f, b3, with_jumps<POIS, DICH>(h1, pj, dg));           // corrector
+        if (CHI) {
+            chi[0] = __fmul_rn(0.5f, b2 - b3);
+            chi[1] = 0.0f;
+        }
     }
     if (FOLD) fold<MODEL>(S);
 }
@@ -380,6 +392,26 @@ __device__ __forceinline__ float gauss_inc(const uint4& w, uint32_t k, const Poi
     }
 }
 
+// Gaussian increment of step n drawn on its own (the chunked loops draw a
+// block's word once for its 16 steps).
+template <int GAUSS>
+__device__ __forceinline__ float gauss_at(const PointConsts& P, const LaunchConsts& K, uint32_t path, uint32_t n)
+{
+    float dxi = 0.0f;
+    if (GAUSS == kGauss3Point) {
+        const uint4 w = stream(K, P.c1_gauss, path, n >> 4);
+        const uint32_t q = (n >> 2) & 3u;
+        uint32_t r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
+        const uint32_t k = n & 3u;
+        r *= k == 0u ? 1u : (k == 1u ? 6u : (k == 2u ? 36u : 216u));
+        dxi = three_point(r, P);
+    } else if (GAUSS == kGaussNormal) {
+        const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
+        dxi = gauss_inc<GAUSS>(w, n & 3u, P);
+    }
+    return dxi;
+}
+
 // Steps n in [n, n_end) one at a time (phase edges that are not whole
 // 32-step chunks).
 template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC>
@@ -387,18 +419,7 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
                                              uint32_t path, uint32_t n, uint32_t n_end)
 {
     for (; n < n_end; ++n) {
-        float dxi = 0.0f;
-        if (GAUSS == kGauss3Point) {
-            const uint4 w = stream(K, P.c1_gauss, path, n >> 4);
-            const uint32_t q = (n >> 2) & 3u;
-            uint32_t r = q == 0u ? w.x : (q == 1u ? w.y : (q == 2u ? w.z : w.w));
-            const uint32_t k = n & 3u;
-            r *= k == 0u ? 1u : (k == 1u ? 6u : (k == 2u ? 36u : 216u));
-            dxi = three_point(r, P);
-        } else if (GAUSS == kGaussNormal) {
-            const uint4 w = stream(K, P.c1_gauss, path, n >> 2);
-            dxi = gauss_inc<GAUSS>(w, n & 3u, P);
-        }
+        const float dxi = gauss_at<GAUSS>(P, K, path, n);
         float pj, dg;
         jumps_inline<POIS, DICH>(S, P, K, path, n, pj, dg);
         pc_step<MODEL, POIS, DICH, ACC, true>(S, P, dxi, pj, dg, drive_at(n, P), drive_at(n + 1u, P));

@@ -38,6 +38,12 @@ cudaError_t launch_segment(int model, bool pois, int dich, int gauss, const Poin
                            const Workspace& ws, const PathOutPtrs& po, int block_threads,
                            int grid_blocks, int sm_count, cudaStream_t st);
 
+// Sec. 4's local-error indicator over steps [0, n_steps) of every path:
+// item partials {paths, sum chi_x^2, sum chi_v^2, max |chi_x|, max |chi_v|}.
+cudaError_t launch_chi(int model, bool pois, int dich, int gauss, const PointConsts& P,
+                       const LaunchConsts& K, uint32_t n_steps, const Workspace& ws, int block_threads,
+                       int grid_blocks, int sm_count, cudaStream_t st);
+
 // Inertial-washboard scan kernel over an item table of (point, first path);
 // gauss is 0 (no Gaussian noise) or the three-point law.
 cudaError_t launch_scan(bool pois, int dich, int gauss, const PointConsts* pts_dev,

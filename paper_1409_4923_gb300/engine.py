@@ -93,6 +93,8 @@ def lib():
         "sde_checkpoint_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
         "sde_checkpoint": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
         "sde_restore": (ctypes.c_int, [_P, _P, ctypes.c_uint64]),
+        "sde_local_error": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_double)]),
         "sde_reduce_f64": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
         "sde_philox_words": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "sde_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
@@ -274,6 +276,13 @@ class Engine:
         out = (Stats * max(n, 1))()
         _check(self._ctx, lib().sde_scan_resume(self._ctx, out, float(deadline_ms)))
         return [out[i].as_dict() for i in range(n)]
+
+    def local_error(self, paths, dt, n_steps):
+        """Sec. 4's chi over paths x n_steps steps: dict of rms and max of chi_x
+        (x units) and chi_v (inertial model)."""
+        o = (ctypes.c_double * 4)()
+        _check(self._ctx, lib().sde_local_error(self._ctx, int(paths), float(dt), int(n_steps), o))
+        return {"rms_x": o[0], "rms_v": o[1], "max_x": o[2], "max_v": o[3]}
 
     def reduce_f64(self, vals):
         """vals: contiguous CUDA float64 tensor -> (n, sum, sum of squares)."""
