@@ -3,7 +3,9 @@
 // The context validates parameters, turns them into FP32/FP64 kernel
 // constants once (in FP64 on the host), owns a grow-only device workspace and
 // a pinned result buffer, and enqueues: counter reset -> persistent path
-// kernel -> fixed-order FP64 fold -> 40-byte device-to-host copy.
+// kernel -> fixed-order FP64 fold -> 40-byte device-to-host copy.  It also
+// runs batched scans (graph-replayed, resumable after a deadline), segmented
+// runs with host checkpoints, and the local-error diagnostic.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -7,6 +7,7 @@ GPU is present, the calls raise.
 """
 import ctypes
 import os
+import struct
 
 import numpy as np
 
@@ -162,6 +163,8 @@ class Engine:
         if rc != SDE_OK:
             raise SdeError(rc, L.sde_last_error(None).decode())
         self.model = model
+        self._seg_paths = 0        # paths of the segmented run (begin / restore)
+        self._scan_n = 0           # points of the last scan (scan_resume)
 
     def close(self):
         if self._ctx:
@@ -231,7 +234,7 @@ class Engine:
         done = ctypes.c_uint64()
         po = None
         if path_out is not None:
-            po = ctypes.byref(self._path_out(path_out, getattr(self, "_seg_paths", 0)))
+            po = ctypes.byref(self._path_out(path_out, self._seg_paths))
         _check(self._ctx, lib().sde_advance(self._ctx, int(n_steps), po, ctypes.byref(done)))
         return done.value
 
@@ -247,7 +250,6 @@ class Engine:
         """Continue the segmented run saved in `data` (from checkpoint())."""
         buf = ctypes.create_string_buffer(bytes(data), len(data))
         _check(self._ctx, lib().sde_restore(self._ctx, buf, len(data)))
-        import struct
         self._seg_paths = struct.unpack_from("<Q", data, 168)[0]   # header field `paths`
 
     def stats(self) -> dict:
@@ -272,7 +274,7 @@ class Engine:
 
     def scan_resume(self, deadline_ms=0.0):
         """Finish the last scan after it raised SdeTimeout (items already done are kept)."""
-        n = getattr(self, "_scan_n", 0)
+        n = self._scan_n
         out = (Stats * max(n, 1))()
         _check(self._ctx, lib().sde_scan_resume(self._ctx, out, float(deadline_ms)))
         return [out[i].as_dict() for i in range(n)]
