@@ -24,3 +24,17 @@ def test_guided_scan_small_grid():
     assert r["validation_max_abs_err"] <= 0.02, r
     assert r["flagged_fraction"] < 0.3, r
     assert r["ratio_plain_over_guided_total"] > 2.0, r
+
+
+def test_box_surrogate_pipeline_small():
+    """The Poisson-box surrogate end to end at a small size: labels from one
+    scan, two networks trained on the device, held-out error below the label
+    spread, timed inference."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import box_surrogate
+    r = box_surrogate.run(n_label=2048, paths=256, steps=1500, n_infer=1 << 14, log=lambda *a: None)
+    assert r["labels"] == 2048 + 256 and r["heldout"] == 256
+    assert r["heldout_v_rmse"] < r["label_v_std"], r
+    assert r["inference_points_per_s"] > 0
+
