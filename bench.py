@@ -270,12 +270,12 @@ def run_engine(args):
         print(json.dumps(line), flush=True)
 
 
-def _oracle_sample(spec, paths):
+def _oracle_sample(spec, paths, threads=None):
     import oracle
     prm = dict(spec["params"])
     prm["noise"] = prm.pop("noise_flags")
     p = oracle.make_params(**prm)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     oracle.run_paths(spec["model"], p, spec["seed"], 0, paths, spec["dt"], spec["n_transient"],
                      spec["n_avg"], nthreads=cores)
@@ -292,9 +292,11 @@ def cpu_baseline(spec, seconds):
     rate = probe * max(1, steps // 20) / t
     paths = max(cores, int(rate * seconds / steps) // cores * cores)
     t, cores = _oracle_sample(spec, paths)
+    t1, _ = _oracle_sample(spec, 2, threads=1)          # one core, as the paper's CPU baseline
     return {"value": paths * steps / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of %d paths, full horizon (%d steps), %.1f s wall" % (
-                paths, spec["paths"], steps, t)}
+                paths, spec["paths"], steps, t),
+            "single_core_value": 2 * steps / t1}
 
 
 def run_reference(args):
