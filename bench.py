@@ -44,7 +44,13 @@ UNIT = "path-steps/s"
 #   event tail: p = 1 - exp(-mu dt) = 0.0127 x (1/4 Philox 10, log 1,
 #   scale 1, floor 1, guard 3, convert 1, state 2 = 19)                 ->  0.24
 ALG_OPS_PER_PATH_STEP = 39.74
-SM_LANES = 128              # FP32 lanes (= issue slots x 32) per SM
+# Issue slots those operations need at the least: GB300 issues the FP32 add,
+# multiply and FMA of two independent paths as one packed-pair instruction,
+# which covers 21 of them (the force and damping FMAs 6, the state updates
+# 10, the fold's scale, subtract and count 3, the window sums 2); the other
+# 18.74 take a slot each.  The ceiling is one slot per lane per clock.
+ALG_SLOTS_PER_PATH_STEP = 39.74 - 21 / 2
+SM_LANES = 128              # issue slots x 32 lanes per SM and clock
 DEFAULT_SM_MHZ = 2070.0
 
 
@@ -222,7 +228,7 @@ def run_engine(args):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak_tops = n_sm * SM_LANES * sm_mhz * 1e6 / 1e12
     kernel_s = statistics.mean(times)
-    achieved = ALG_OPS_PER_PATH_STEP * units / kernel_s / 1e12
+    achieved = ALG_SLOTS_PER_PATH_STEP * units / kernel_s / 1e12
     traffic = _profile_traffic(args.workload)
     st = results[-1]
     line = {
@@ -244,10 +250,11 @@ def run_engine(args):
                                     "steps_per_launch": knobs["steps_per_launch"] or "whole run",
                                     "chosen_by": "fixed" if args.no_autotune else "autotuner"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops,
-                     "unit": "Top/s (lane ops)", "frac": achieved / peak_tops,
+                     "unit": "T issue slots/s (lane)", "frac": achieved / peak_tops,
                      "traffic": traffic,
                      "peak_basis": "%d SMs x %d lanes x %.0f MHz (%s sm_max_mhz)" % (
                          n_sm, SM_LANES, sm_mhz, peak_kind),
+                     "alg_slots_per_path_step": ALG_SLOTS_PER_PATH_STEP,
                      "alg_ops_per_path_step": ALG_OPS_PER_PATH_STEP},
         # host->device: the parameter record and the fold's item range;
         # device->host: five FP64 sums and the status word

@@ -703,6 +703,119 @@ __device__ __forceinline__ bool chunk_events_multi(PathState (&S)[PPT], const Po
     return true;
 }
 
+// Two inertial paths per lane on the packed FP32 pair instructions of sm_100
+// and later (__ffma2_rn, __fadd2_rn, __fmul2_rn: per component exactly
+// __fmaf_rn, __fadd_rn, __fmul_rn).  Component x is path 0, y path 1; every
+// operation of pc_step, fold and accumulate is applied to the pair in the same
+// order, so each path takes the arithmetic of one path per lane bit for bit,
+// while the step issues about half as many FP32 instructions.  The SFU
+// cosines, the three-point draws and the jump selections stay per path.  The
+// chunk is two 16-step blocks as in chunk_steps.
+__device__ __forceinline__ float2 cos2_sfu(float2 x) { return make_float2(cos_sfu(x.x), cos_sfu(x.y)); }
+
+template <bool POIS, int DICH>
+__device__ __forceinline__ float2 with_jumps2(float2 h1, float2 pj, float2 dg)
+{
+    if (DICH == 1) return POIS ? __fadd2_rn(h1, __fadd2_rn(pj, dg)) : __fadd2_rn(h1, dg);
+    return POIS ? __fadd2_rn(h1, pj) : h1;
+}
+
+template <bool POIS, int DICH, int GAUSS, bool ACC>
+__device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointConsts& P,
+                                               const LaunchConsts& K, const uint32_t (&path)[2],
+                                               uint32_t n0, float dch, float& dcur, uint4 (&w)[2],
+                                               uint32_t (&pm)[2], float (&z0)[2], float (&z1)[2],
+                                               float (&z2)[2], uint32_t (&dm)[2])
+{
+    const float2 ngdt = make_float2(-P.gdt, -P.gdt), nfdt = make_float2(-P.fdt, -P.fdt);
+    const float2 wdt = make_float2(P.wdt, P.wdt), whdt = make_float2(P.whdt, P.whdt);
+    const float2 half = make_float2(0.5f, 0.5f);
+    float2 c = make_float2(S[0].c, S[1].c), v = make_float2(S[0].v, S[1].v);
+    float2 kf = make_float2(S[0].kf, S[1].kf);
+    float2 sv = make_float2(S[0].sv, S[1].sv), sv2 = make_float2(S[0].sv2, S[1].sv2);
+#pragma unroll 1
+    for (uint32_t b = 0; b < 2u; ++b) {
+        uint4 wn[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            wn[p] = make_uint4(0u, 0u, 0u, 0u);
+            if (GAUSS == kGauss3Point) wn[p] = stream(K, P.c1_gauss, path[p], (n0 >> 4) + b + 1u);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4u; ++q) {
+            uint32_t r[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                r[p] = q == 0u ? w[p].x : (q == 1u ? w[p].y : (q == 2u ? w[p].z : w[p].w));
+#pragma unroll
+            for (uint32_t k = 0; k < 4u; ++k) {
+                const float dnext = __shfl_sync(0xffffffffu, dch, (int)(q * 4u + k));
+                const uint32_t bit = 1u << (q * 4u + k);
+                float2 dxi = make_float2(0.0f, 0.0f), pj = dxi, dg = dxi;
+                if (GAUSS == kGauss3Point) {
+                    dxi.x = three_point(r[0], P);
+                    dxi.y = three_point(r[1], P);
+                }
+                if (POIS) {
+                    float pv[2];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const bool kick = (pm[p] & bit) != 0u;
+                        pv[p] = kick ? z0[p] : -P.aP_dt;
+                        z0[p] = kick ? z1[p] : z0[p];
+                        z1[p] = kick ? z2[p] : z1[p];
+                    }
+                    pj = make_float2(pv[0], pv[1]);
+                }
+                if (DICH) {
+                    dg.x = (dm[0] & bit) != 0u ? P.Fb_dt : P.mFa_dt;
+                    dg.y = (dm[1] & bit) != 0u ? P.Fb_dt : P.mFa_dt;
+                }
+                float2 d0 = make_float2(dcur, dcur), d1 = make_float2(dnext, dnext);
+                if (DICH == 2) {
+                    d0 = __fadd2_rn(d0, dg);
+                    d1 = __fadd2_rn(d1, dg);
+                }
+                // Algorithm 1 on (x, v), as pc_step
+                const float2 b1 = __ffma2_rn(nfdt, cos2_sfu(c), __ffma2_rn(ngdt, v, d0));
+                const float2 vxi = __fadd2_rn(v, dxi);
+                float2 cb = __ffma2_rn(wdt, v, c);
+                float2 vb = __fadd2_rn(vxi, b1);
+                const float2 b2 = __ffma2_rn(nfdt, cos2_sfu(cb), __ffma2_rn(ngdt, vb, d1));
+                const float2 ch = __ffma2_rn(whdt, v, c);
+                const float2 h1 = __ffma2_rn(half, b1, vxi);
+                cb = __ffma2_rn(whdt, vb, ch);
+                vb = __ffma2_rn(half, b2, h1);
+                const float2 b3 = __ffma2_rn(nfdt, cos2_sfu(cb), __ffma2_rn(ngdt, vb, d1));
+                c = __ffma2_rn(whdt, vb, ch);
+                v = __ffma2_rn(half, b3, with_jumps2<POIS, DICH>(h1, pj, dg));
+                if (ACC) {
+                    sv = __fadd2_rn(sv, v);
+                    sv2 = __ffma2_rn(v, v, sv2);
+                }
+                dcur = dnext;
+            }
+            // fold, as fold<kModelInertial>
+            const float2 t = __fmul2_rn(c, make_float2(0.15915494309189535f, 0.15915494309189535f));
+            const float2 rr = make_float2(rintf(t.x), rintf(t.y));
+            c = __ffma2_rn(make_float2(-6.2831853071795865f, -6.2831853071795865f), rr, c);
+            kf = __fadd2_rn(kf, rr);
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            w[p] = wn[p];
+            pm[p] >>= 16;
+            dm[p] >>= 16;
+        }
+        dch = __shfl_down_sync(0xffffffffu, dch, 16);   // the second block's drive values
+    }
+    S[0].c = c.x; S[1].c = c.y;
+    S[0].v = v.x; S[1].v = v.y;
+    S[0].kf = kf.x; S[1].kf = kf.y;
+    S[0].sv = sv.x; S[1].sv = sv.y;
+    S[0].sv2 = sv2.x; S[1].sv2 = sv2.y;
+}
+
 template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST, int PPT>
 __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const PointConsts& P,
                                                   const LaunchConsts& K, const uint32_t (&path)[PPT],
@@ -710,6 +823,10 @@ __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const Poi
                                                   uint32_t (&pm)[PPT], float (&z0)[PPT], float (&z1)[PPT],
                                                   float (&z2)[PPT], uint32_t (&dm)[PPT])
 {
+    if constexpr (PPT == 2 && MODEL == kModelInertial && GAUSS != kGaussNormal && (!POIS || FAST)) {
+        chunk_steps_x2<POIS, DICH, GAUSS, ACC>(S, P, K, path, n0, dch, dcur, w, pm, z0, z1, z2, dm);
+        return;
+    }
     uint4 wn[PPT];
 #pragma unroll 1
     for (uint32_t g = 0; g < 8u; ++g) {

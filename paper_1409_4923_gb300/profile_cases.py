@@ -1,6 +1,6 @@
 """Small, self-contained launches for profiling the engine's kernels.
 
-  python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800
+  python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800 [--ppt 2]
   python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576 --path 1
   python -m paper_1409_4923_gb300.profile_cases scan --points 256
 
@@ -23,11 +23,13 @@ def main():
     ap.add_argument("--rows", type=int, default=1 << 20)
     ap.add_argument("--points", type=int, default=256)
     ap.add_argument("--path", type=int, default=1, help="mlp: 1 tcgen05, 0 mma.sync")
+    ap.add_argument("--ppt", type=int, default=1, help="point: paths per lane (1 or 2)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.case == "point":
         spec = W.run_spec(a.workload)
         eng = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"])
+        eng.set_paths_per_thread(a.ppt)
         for _ in range(2):
             eng.run(a.paths, spec["dt"], 0, a.steps)
             print("mean_v", eng.stats()["mean_v"])
