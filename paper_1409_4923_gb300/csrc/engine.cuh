@@ -741,7 +741,10 @@ __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointCon
             wn[p] = make_uint4(0u, 0u, 0u, 0u);
             if (GAUSS == kGauss3Point) wn[p] = stream(K, P.c1_gauss, path[p], (n0 >> 4) + b + 1u);
         }
-#pragma unroll
+        // With Poisson noise the block keeps one 4-step group per iteration:
+        // the two paths' kick queues unrolled over 16 steps overflow the
+        // instruction cache (measured: half speed, "no instruction" stalls).
+#pragma unroll (POIS ? 1 : 4)
         for (uint32_t q = 0; q < 4u; ++q) {
             uint32_t r[2];
 #pragma unroll
