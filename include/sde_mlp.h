@@ -71,6 +71,24 @@ int sde_mlp_gradients(sde_mlp* net, const float* x, const float* t, uint64_t M,
 int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M, float lr,
                        float beta1, float beta2, float eps, float* loss_dev);
 
+/* Adam training on the device: `steps` steps on minibatches of `batch` rows
+ * of the labels X (device, N x 7 FP32 raw inputs) and T (device, N x 2 FP32
+ * targets), the loss of sde_mlp_gradients.  Rows are visited in epochs of
+ * N / batch whole minibatches, each epoch in a fresh order: a bijection of
+ * [0, N) keyed by (seed, epoch), a four-round Feistel network with cycle
+ * walking.  The learning rate decays from lr to lr_final along a half cosine,
+ * lr_k = lr_final + (lr - lr_final)(1 + cos(pi k / (steps - 1))) / 2; Adam's
+ * bias corrections continue the network's step count (earlier
+ * sde_mlp_train_step or sde_mlp_fit calls).  losses (device, `steps` floats,
+ * or NULL) receives each step's minibatch loss before its update.  One step is
+ * captured as a CUDA graph on a private stream and replayed, ordered after
+ * the work already on the network's stream; returns when the steps are done.
+ * Requires 1 <= batch <= min(N, 65536), N <= 2^30, steps >= 1 (else
+ * SDE_EINVAL). */
+int sde_mlp_fit(sde_mlp* net, const float* X, const float* T, uint64_t N, uint64_t steps,
+                uint32_t batch, float lr, float lr_final, float beta1, float beta2, float eps,
+                uint64_t seed, float* losses);
+
 /* Matrix path of the forward pass: 1 (default) two fused kernels on the
  * fifth-generation tensor cores (input map and layers 1-2; layers 3-4 and
  * the output map; tcgen05.mma with FP32 accumulators in tensor memory,

@@ -110,36 +110,50 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
 
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        // ---- stage A and B (2 x 16-byte chunks per thread each)
+    // ---- staging of A and B (2 x 16-byte chunks per thread each): the next
+    // K tile is fetched into registers while the current one is multiplied
+    uint4 va[2], ub[2];
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int c = tid; c < 256; c += 128) {
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        for (int j = 0; j < 2; ++j) {
+            const int c = tid + 128 * j;
+            va[j] = make_uint4(0u, 0u, 0u, 0u);
+            ub[j] = make_uint4(0u, 0u, 0u, 0u);
             if (!A_KM) {
                 const int r = c >> 2, col = (c & 3) * 8;
                 const int gm = m0 + r, gk = k0 + col;
-                if (gm < g.M && gk < ke) v = *(const uint4*)(g.A + (size_t)gm * g.lda + gk);
-                *(uint4*)&sA[r][col] = v;
+                if (gm < g.M && gk < ke) va[j] = *(const uint4*)(g.A + (size_t)gm * g.lda + gk);
             } else {
                 const int r = c >> 3, col = (c & 7) * 8;
                 const int gk = k0 + r, gm = m0 + col;
-                if (gk < ke && gm < g.M) v = *(const uint4*)(g.A + (size_t)gk * g.lda + gm);
-                *(uint4*)&sA[r][col] = v;
+                if (gk < ke && gm < g.M) va[j] = *(const uint4*)(g.A + (size_t)gk * g.lda + gm);
             }
-            uint4 u = make_uint4(0u, 0u, 0u, 0u);
             if (!B_KN) {
                 const int r = c >> 2, col = (c & 3) * 8;
                 const int gn = n0 + r, gk = k0 + col;
-                if (gn < g.N && gk < ke) u = *(const uint4*)(g.B + (size_t)gn * g.ldb + gk);
-                *(uint4*)&sB[r][col] = u;
+                if (gn < g.N && gk < ke) ub[j] = *(const uint4*)(g.B + (size_t)gn * g.ldb + gk);
             } else {
                 const int r = c >> 3, col = (c & 7) * 8;
                 const int gk = k0 + r, gn = n0 + col;
-                if (gk < ke && gn < g.N) u = *(const uint4*)(g.B + (size_t)gk * g.ldb + gn);
-                *(uint4*)&sB[r][col] = u;
+                if (gk < ke && gn < g.N) ub[j] = *(const uint4*)(g.B + (size_t)gk * g.ldb + gn);
             }
         }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = tid + 128 * j;
+            if (!A_KM) *(uint4*)&sA[c >> 2][(c & 3) * 8] = va[j];
+            else *(uint4*)&sA[c >> 3][(c & 7) * 8] = va[j];
+            if (!B_KN) *(uint4*)&sB[c >> 2][(c & 3) * 8] = ub[j];
+            else *(uint4*)&sB[c >> 3][(c & 7) * 8] = ub[j];
+        }
+    };
+    if (kb < ke) fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        stash();
         __syncthreads();
+        if (k0 + BK < ke) fetch(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t af[2][4];
@@ -292,15 +306,30 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int splits, 
     out[i] = s;
 }
 
-// Column sums of a BF16 [Mp][N] matrix (bias gradients), one thread per column.
-__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ G, uint64_t Mp, int N, int ld,
-                              float* __restrict__ out)
+// Column sums of a BF16 [Mp][N] matrix (bias gradients).  A block of 32 x 8
+// threads takes 32 columns: thread (c, r) sums rows r, r + 8, ... of column c
+// in order, then the eight partials of each column are added in order of r.
+constexpr int kColsumRows = 8;
+
+__global__ void __launch_bounds__(32 * kColsumRows) colsum_kernel(const __nv_bfloat16* __restrict__ G, uint64_t Mp,
+                                                                  int N, int ld, float* __restrict__ out)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float part[kColsumRows][32];
+    const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + c;
     float s = 0.0f;
-    for (uint64_t m = 0; m < Mp; ++m) s += __bfloat162float(G[m * ld + n]);
-    out[n] = s;
+    if (n < N) {
+#pragma unroll 8
+        for (uint64_t m = (uint64_t)r; m < Mp; m += kColsumRows) s += __bfloat162float(G[m * ld + n]);
+    }
+    part[r][c] = s;
+    __syncthreads();
+    if (r == 0 && n < N) {
+        float t = part[0][c];
+#pragma unroll
+        for (int q = 1; q < kColsumRows; ++q) t += part[q][c];
+        out[n] = t;
+    }
 }
 
 // Adam on the flat FP32 parameters; refreshes the BF16 copies.
@@ -318,6 +347,103 @@ __global__ void adam_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ w
     const float wi = w[i] - lr * (a * c1) / (sqrtf(b * c2) + eps);
     w[i] = wi;
     wb[i] = __float2bfloat16_rn(wi);
+}
+
+// ---- training loop on the device (sde_mlp_fit): one step is captured once as
+// a CUDA graph and replayed; everything that changes between steps is read
+// from FitState in device memory.
+
+struct FitState {
+    unsigned long long k;   // steps done
+};
+
+__device__ __forceinline__ uint32_t mix32(uint32_t h)
+{
+    h ^= h >> 16; h *= 0x7FEB352Du;
+    h ^= h >> 15; h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+
+// Row of position `pos` in the shuffled order of an epoch: a four-round
+// Feistel network keyed by (seed, epoch) permutes [0, 2^bits) (bits even,
+// 2^bits >= N), and positions that land at or above N walk on along their
+// cycle until they fall below N.  The walk ends because the cycle through pos
+// returns to pos < N; 2^bits < 4N makes it short on average.  The result is a
+// bijection of [0, N).
+__device__ __forceinline__ uint32_t shuffle_row(uint32_t pos, uint32_t N, uint32_t bits,
+                                                unsigned long long seed, unsigned long long epoch)
+{
+    const uint32_t half = bits >> 1, mask = (1u << half) - 1u;
+    uint32_t key[4];
+    unsigned long long z = seed * 0x9E3779B97F4A7C15ull + epoch * 0xD1B54A32D192ED03ull;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        z += 0x9E3779B97F4A7C15ull;
+        unsigned long long y = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        y = (y ^ (y >> 27)) * 0x94D049BB133111EBull;
+        key[r] = (uint32_t)(y ^ (y >> 31));
+    }
+    uint32_t x = pos;
+    for (uint32_t it = 0; it <= (1u << bits); ++it) {
+        uint32_t L = x >> half, R = x & mask;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t F = mix32(R ^ key[r]) & mask;
+            const uint32_t nL = R;
+            R = L ^ F;
+            L = nL;
+        }
+        x = (L << half) | R;
+        if (x < N) break;
+    }
+    return x;
+}
+
+// The step's minibatch: rows of positions [s batch, (s + 1) batch) of epoch
+// k / per_epoch's order (s = k mod per_epoch), copied into xb, tb.
+__global__ void fit_gather_kernel(const FitState* __restrict__ fs, const float* __restrict__ X,
+                                  const float* __restrict__ T, uint32_t N, uint32_t batch, uint32_t per_epoch,
+                                  uint32_t bits, unsigned long long seed, float* __restrict__ xb,
+                                  float* __restrict__ tb)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    const unsigned long long k = fs->k;
+    const uint32_t pos = (uint32_t)(k % per_epoch) * batch + i;
+    const uint32_t row = shuffle_row(pos, N, bits, seed, k / per_epoch);
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) xb[(size_t)i * kIn + c] = X[(size_t)row * kIn + c];
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) tb[(size_t)i * kOut + o] = T[(size_t)row * kOut + o];
+}
+
+// Adam as adam_kernel with step k's learning rate and bias corrections from
+// the table sched (lr, c1, c2 per step).
+__global__ void adam_fit_kernel(float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
+                                float* __restrict__ m1, float* __restrict__ m2, size_t n,
+                                const FitState* __restrict__ fs, const float* __restrict__ sched, float b1,
+                                float b2, float eps)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* sk = sched + 3ull * fs->k;
+    const float lr = sk[0], c1 = sk[1], c2 = sk[2];
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    const float wi = w[i] - lr * (a * c1) / (sqrtf(b * c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+}
+
+// Record the step's loss and advance the step counter.
+__global__ void fit_end_kernel(FitState* fs, const float* __restrict__ loss, float* __restrict__ losses)
+{
+    if (losses) losses[fs->k] = *loss;
+    fs->k += 1ull;
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, size_t n)
@@ -484,7 +610,7 @@ static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_
     // layer 4
     if (e == cudaSuccess) e = weight_grad(n, n->dY, kOutPad, kOutPad, n->A[2], kH, kH, Mp, n->grad + oW4);
     if (e == cudaSuccess) {
-        colsum_kernel<<<1, 256, 0, n->stream>>>(n->dY, Mp, kOutPad, kOutPad, n->grad + oB4);
+        colsum_kernel<<<1, 32 * kColsumRows, 0, n->stream>>>(n->dY, Mp, kOutPad, kOutPad, n->grad + oB4);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -500,7 +626,7 @@ static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_
         const int kin = l == 0 ? kInPad : kH;
         e = weight_grad(n, n->dH[l], kH, kH, below, kin, kin, Mp, n->grad + oW[l]);
         if (e == cudaSuccess) {
-            colsum_kernel<<<1, 256, 0, n->stream>>>(n->dH[l], Mp, kH, kH, n->grad + oB[l]);
+            colsum_kernel<<<kH / 32, 32 * kColsumRows, 0, n->stream>>>(n->dH[l], Mp, kH, kH, n->grad + oB[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && l > 0) {
@@ -696,6 +822,102 @@ int sde_mlp_train_step(sde_mlp* n, const float* x, const float* t, uint64_t M, f
     adam_kernel<<<nblk(kNParams), 256, 0, n->stream>>>(n->w, n->wb, n->grad, n->m1, n->m2, kNParams, lr, beta1,
                                                         beta2, eps, c1, c2);
     MLP_CUDA(n, cudaGetLastError());
+    return SDE_OK;
+}
+
+// One training step on the device (gathered minibatch, forward, loss and
+// gradients, Adam with step k's entry of sched), enqueued on n->stream.
+static cudaError_t fit_step(sde_mlp* n, FitState* fs, const float* sched, const float* X, const float* T,
+                            uint32_t N, uint32_t batch, uint32_t per_epoch, uint32_t bits, unsigned long long seed,
+                            float beta1, float beta2, float eps, float* xb, float* tb, float* loss, float* losses)
+{
+    const uint64_t Mp = pad64(batch);
+    fit_gather_kernel<<<nblk(batch), 256, 0, n->stream>>>(fs, X, T, N, batch, per_epoch, bits, seed, xb, tb);
+    input_map_kernel<<<nblk(Mp * kInPad), 256, 0, n->stream>>>(xb, batch, Mp, n->maps, n->log_mask, n->X);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_rows(n, Mp, true);
+    if (e == cudaSuccess) e = backward_rows(n, tb, batch, Mp, loss);
+    if (e != cudaSuccess) return e;
+    adam_fit_kernel<<<nblk(kNParams), 256, 0, n->stream>>>(n->w, n->wb, n->grad, n->m1, n->m2, kNParams, fs, sched,
+                                                            beta1, beta2, eps);
+    fit_end_kernel<<<1, 1, 0, n->stream>>>(fs, loss, losses);
+    return cudaGetLastError();
+}
+
+int sde_mlp_fit(sde_mlp* n, const float* X, const float* T, uint64_t N, uint64_t steps, uint32_t batch,
+                float lr, float lr_final, float beta1, float beta2, float eps, uint64_t seed, float* losses)
+{
+    if (!n) return SDE_EINVAL;
+    if (!X || !T || N == 0 || N > (1ull << 30) || steps == 0 || steps > (1ull << 26) || batch == 0 ||
+        batch > kMaxBatch || batch > N)
+        return mfail(n, SDE_EINVAL,
+                     "bad fit arguments (1 <= batch <= min(N, 65536), N <= 2^30, 1 <= steps <= 2^26)");
+    if (!(lr > 0.0f) || !(lr_final > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        return mfail(n, SDE_EINVAL, "bad Adam hyper-parameters");
+    int rc = ensure_acts(n, pad64(batch), true);
+    if (rc) return rc;
+    uint32_t bits = 2;
+    while ((1ull << bits) < N) bits += 2;
+    const uint32_t per_epoch = (uint32_t)(N / batch);
+    // per-step learning rate (half-cosine decay) and Adam's bias corrections,
+    // in the arithmetic of sde_mlp_train_step
+    std::vector<float> sched(3 * steps);
+    const double pi = 3.14159265358979323846;
+    for (uint64_t k = 0; k < steps; ++k) {
+        const double frac = steps > 1 ? (double)k / (double)(steps - 1) : 0.0;
+        sched[3 * k] = (float)((double)lr_final + 0.5 * ((double)lr - (double)lr_final) * (1.0 + std::cos(pi * frac)));
+        const double t = (double)(n->step + k + 1);
+        sched[3 * k + 1] = (float)(1.0 / (1.0 - std::pow((double)beta1, t)));
+        sched[3 * k + 2] = (float)(1.0 / (1.0 - std::pow((double)beta2, t)));
+    }
+    // scratch: FitState, the step's loss, the gathered minibatch, the schedule
+    const size_t off_x = 64, off_t = off_x + ((size_t)batch * kIn * 4 + 255) / 256 * 256;
+    const size_t off_s = off_t + ((size_t)batch * kOut * 4 + 255) / 256 * 256;
+    const size_t bytes = off_s + sched.size() * 4;
+    char* scratch = nullptr;
+    MLP_CUDA(n, cudaMalloc(&scratch, bytes));
+    FitState* fs = (FitState*)scratch;
+    float* loss = (float*)(scratch + 32);
+    float* xb = (float*)(scratch + off_x);
+    float* tb = (float*)(scratch + off_t);
+    float* dsched = (float*)(scratch + off_s);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const cudaStream_t user = n->stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 64, user);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dsched, sched.data(), sched.size() * 4, cudaMemcpyHostToDevice, user);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        n->stream = cs;
+        cudaError_t ec = fit_step(n, fs, dsched, X, T, (uint32_t)N, batch, per_epoch, bits, seed, beta1, beta2,
+                                  eps, xb, tb, loss, losses);
+        n->stream = user;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (ec != cudaSuccess) e = ec;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    for (uint64_t k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, ev, 0);
+    const cudaError_t es = cs ? cudaStreamSynchronize(cs) : cudaSuccess;
+    if (e == cudaSuccess) e = es;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    const cudaError_t eu = cudaStreamSynchronize(user);     // the schedule upload used `sched`
+    if (e == cudaSuccess) e = eu;
+    cudaFree(scratch);
+    MLP_CUDA(n, e);
+    n->step += steps;
     return SDE_OK;
 }
 

@@ -209,7 +209,7 @@ class DichotGuidedScan:
 
 def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=4096, rerun_paths=8192,
                        spp=200, transient=200, periods=2000, tol=0.01, se_tol=0.005, n_valid=2048,
-                       seed=0, steps=32000, valid_stream=13, coverage=0.999, log=print):
+                       seed=0, steps=64000, valid_stream=13, coverage=0.999, log=print):
     """The surrogate-guided scan against plain Monte Carlo on a random sample of
     the same grid points (see the module docstring)."""
     import torch
@@ -281,7 +281,7 @@ def main():
     ap.add_argument("--periods", type=int, default=2000)
     ap.add_argument("--transient", type=int, default=200)
     ap.add_argument("--valid", type=int, default=4096)
-    ap.add_argument("--steps", type=int, default=32000)
+    ap.add_argument("--steps", type=int, default=64000)
     ap.add_argument("--coverage", type=float, default=0.999)
     a = ap.parse_args()
     torch.cuda.set_device(0)

@@ -3,6 +3,7 @@
   python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800 [--ppt 2]
   python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576 --path 1
   python -m paper_1409_4923_gb300.profile_cases scan --points 256
+  python -m paper_1409_4923_gb300.profile_cases fit --rows 16384 --steps 200
 
 Each case runs its launch twice (a warm-up and the one to capture) and
 prints a checksum, so `ncu -s 1 -c 1 -k <kernel>` captures a warm launch.
@@ -16,7 +17,7 @@ def main():
     import torch
     from . import engine as E, workloads as W
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["point", "mlp", "scan"])
+    ap.add_argument("case", choices=["point", "mlp", "scan", "fit"])
     ap.add_argument("workload", nargs="?", default="dichot_2p20")
     ap.add_argument("--paths", type=int, default=1 << 20)
     ap.add_argument("--steps", type=int, default=800)
@@ -24,6 +25,7 @@ def main():
     ap.add_argument("--points", type=int, default=256)
     ap.add_argument("--path", type=int, default=1, help="mlp: 1 tcgen05, 0 mma.sync")
     ap.add_argument("--ppt", type=int, default=1, help="point: paths per lane (1 or 2)")
+    ap.add_argument("--batch", type=int, default=512, help="fit: minibatch rows")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.case == "point":
@@ -44,6 +46,16 @@ def main():
             y = net.forward(x)
             net.sync()
             print("checksum", float(y.double().sum()))
+        net.close()
+    elif a.case == "fit":
+        from . import surrogate as S
+        rng = np.random.default_rng(0)
+        x = torch.from_numpy(rng.uniform(0.5, 1.5, (a.rows, 7)).astype(np.float32)).cuda()
+        t = torch.from_numpy(rng.normal(0.0, 1.0, (a.rows, 2)).astype(np.float32)).cuda()
+        net = S.Surrogate(0)
+        for _ in range(2):
+            hist = net.fit(x, t, steps=a.steps, batch=a.batch)
+            print("loss first/last", float(hist[0]), float(hist[-1]))
         net.close()
     else:
         pts = W.scan_64x64()[:a.points]

@@ -31,6 +31,8 @@ def _lib():
             "sde_mlp_gradients": (ctypes.c_int, [P, P, P, ctypes.c_uint64, P,
                                                  ctypes.POINTER(ctypes.c_double)]),
             "sde_mlp_train_step": (ctypes.c_int, [P, P, P, ctypes.c_uint64, f, f, f, f, P]),
+            "sde_mlp_fit": (ctypes.c_int, [P, P, P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                           f, f, f, f, f, ctypes.c_uint64, P]),
             "sde_mlp_gemm_bf16": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
                                                  ctypes.c_uint32, ctypes.c_uint32, P, ctypes.c_uint32,
                                                  P, ctypes.c_uint32, P, ctypes.c_uint32]),
@@ -122,27 +124,21 @@ class Surrogate:
             self._net, _ptr(x), _ptr(t), x.shape[0], float(lr), float(beta1), float(beta2),
             float(eps), _ptr(loss_out) if loss_out is not None else None))
 
-    def fit(self, X, T, steps=8000, batch=512, lr=2e-3, lr_final=2e-5, seed=0):
+    def fit(self, X, T, steps=8000, batch=512, lr=2e-3, lr_final=2e-5, seed=0,
+            beta1=0.9, beta2=0.999, eps=1e-8):
         """Adam with a cosine learning-rate decay over `steps` minibatches drawn
-        (device-side) from shuffled epochs.  X, T: CUDA float32 [N, 7] and [N, 2].
-        Returns the batch losses (numpy, one per step)."""
+        (on the device) from epochs in shuffled order, the whole loop in one
+        sde_mlp_fit call.  X, T: CUDA float32 [N, 7] and [N, 2].  Returns the
+        batch losses (numpy, one per step)."""
         import torch
+        X = X.contiguous()
+        T = T.contiguous()
         n = X.shape[0]
         batch = min(batch, n)
-        g = torch.Generator(device=X.device)
-        g.manual_seed(seed)
-        per_epoch = max(1, n // batch)
         losses = torch.zeros(steps, dtype=torch.float32, device=X.device)
-        perm = None
-        for k in range(steps):
-            s = k % per_epoch
-            if s == 0:
-                perm = torch.randperm(n, device=X.device, generator=g)
-            idx = perm[s * batch:(s + 1) * batch]
-            xb = X.index_select(0, idx)
-            tb = T.index_select(0, idx)
-            lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
-            self.train_step(xb, tb, lr_k, loss_out=losses[k:k + 1])
+        self._check(self._L.sde_mlp_fit(self._net, _ptr(X), _ptr(T), n, int(steps), int(batch), float(lr),
+                                        float(lr_final), float(beta1), float(beta2), float(eps), int(seed),
+                                        _ptr(losses)))
         return losses.cpu().numpy()
 
     def gemm_bf16(self, a_layout, b_layout, M, N, K, A, B):

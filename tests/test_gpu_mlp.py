@@ -169,6 +169,57 @@ def test_training_fits_a_smooth_function(S):
     assert np.all(rmse < 0.15), rmse
 
 
+def _cosine_lr(lr, lr_final, k, steps):
+    return lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+
+
+def test_fit_full_batch_matches_train_steps(S):
+    """sde_mlp_fit with one minibatch per epoch (batch = N) against as many
+    sde_mlp_train_step calls on the rows in their natural order, with the host's
+    cosine learning rates.  The epoch's shuffled order must be a permutation of
+    the rows (the loss before the first update is the full-data loss; a
+    duplicated or missing row would move it by about 1/N), and the graph-replayed
+    schedule and Adam corrections those of the host loop.  Only the summation
+    order of the gradients' row reductions differs."""
+    rng = np.random.default_rng(21)
+    N, steps, lr, lr_final = 200, 6, 2e-3, 2e-4
+    x = torch.from_numpy(_raw_inputs(rng, N).astype(np.float32)).cuda()
+    t = torch.from_numpy(np.stack([rng.normal(0.1, 0.2, N), rng.normal(-3.0, 1.5, N)],
+                                  axis=1).astype(np.float32)).cuda()
+    nets = [_random_net(S, 22)[0] for _ in range(2)]
+    try:
+        hist = nets[0].fit(x, t, steps=steps, batch=N, lr=lr, lr_final=lr_final, seed=5)
+        ref = torch.zeros(steps, dtype=torch.float32, device="cuda")
+        for k in range(steps):
+            nets[1].train_step(x, t, _cosine_lr(lr, lr_final, k, steps), loss_out=ref[k:k + 1])
+        ref = ref.cpu().numpy()
+        pa = nets[0].get_params().astype(np.float64)
+        pb = nets[1].get_params().astype(np.float64)
+    finally:
+        for n in nets:
+            n.close()
+    np.testing.assert_allclose(hist[0], ref[0], rtol=1e-6)
+    np.testing.assert_allclose(hist, ref, rtol=1e-5)
+    assert hist[-1] < hist[0]
+    # parameters: equal up to the reduction order (a weight whose gradient is
+    # at rounding level may take Adam's sign step the other way)
+    assert np.mean(np.abs(pa - pb) > 1e-5) < 0.01
+
+
+def test_fit_rejects_bad_arguments(S):
+    net = S.Surrogate(3)
+    try:
+        x = torch.zeros((16, 7), dtype=torch.float32, device="cuda")
+        t = torch.zeros((16, 2), dtype=torch.float32, device="cuda")
+        for kw in (dict(steps=0), dict(lr=0.0), dict(lr_final=-1.0)):
+            with pytest.raises(Exception):
+                net.fit(x, t, **dict(dict(steps=2, batch=8), **kw))
+        rc = net._L.sde_mlp_fit(net._net, S._ptr(x), S._ptr(t), 16, 2, 17, 1e-3, 1e-4, 0.9, 0.999, 1e-8, 0, None)
+        assert rc != 0                                           # batch > N
+    finally:
+        net.close()
+
+
 def test_tcgen05_forward_matches_mma_path_and_oracle(S):
     """The fused tcgen05 forward (maps and layers 1-2; layers 3-4 and the
     output map; FP32 accumulators in tensor memory, two per CTA) against the
