@@ -134,8 +134,10 @@ def tune(model, params, dt, paths, n_probe_steps=2048, seed=0, stream=None, cach
     return dict(res, seconds=shapes, seconds_steps_per_launch=spl)
 
 
-def scan_key(device_name, model, flags):
-    return "%s|scan|model=%d|flags=%d" % (device_name, model, flags)
+def scan_key(device_name, model, flags, items):
+    """Cache key of a scan shape: a shape tuned on a few hundred 32-path items
+    (a fixed grid of one wave can win there) must not serve a scan of 10^5."""
+    return "%s|scan|model=%d|flags=%d|items~4^%d" % (device_name, model, flags, size_class(items))
 
 
 def tune_scan(model, points, seed=0, n_probe_points=256, probe_steps=4096, stream=None, cache=None,
@@ -143,13 +145,14 @@ def tune_scan(model, points, seed=0, n_probe_points=256, probe_steps=4096, strea
     """Launch shape of the batched scan: time every (block, grid) candidate on a
     probe scan of the first n_probe_points points, each cut to probe_steps
     steps (one persistent launch per candidate), and cache the fastest per
-    (device, model, noise flags).  Paths per lane and steps per launch do not
+    (device, model, noise flags, size class of the points' 32-path items).  Paths per lane and steps per launch do not
     apply to the scan kernel.  Returns dict(block, grid)."""
     import torch
     cache = cache or cache_path()
     dev = torch.cuda.get_device_name(torch.cuda.current_device())
     flags = points[0]["params"].noise_flags
-    k = scan_key(dev, model, flags)
+    items = sum((int(p["paths"]) + 31) // 32 for p in points)
+    k = scan_key(dev, model, flags, items)
     data = _load(cache)
     if not force and k in data:
         return {"block": data[k]["block"], "grid": data[k]["grid"]}
