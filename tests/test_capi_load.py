@@ -68,6 +68,17 @@ def test_null_context_calls(lib):
     lib.sde_destroy(None)
 
 
+def test_surrogate_calls_reject_a_null_network(lib):
+    from paper_1409_4923_gb300 import engine as E, surrogate as S
+    L = S._lib()
+    f = ctypes.c_float
+    assert L.sde_mlp_fit(None, None, None, 16, 2, 8, f(1e-3), f(1e-4), f(0.9), f(0.999), f(1e-8), 0,
+                         None) == E.SDE_EINVAL
+    assert L.sde_mlp_train_step(None, None, None, 8, f(1e-3), f(0.9), f(0.999), f(1e-8), None) == E.SDE_EINVAL
+    assert L.sde_mlp_forward(None, None, 8, None) == E.SDE_EINVAL
+    assert L.sde_mlp_create(None, 0, None) == E.SDE_EINVAL
+
+
 def test_engine_has_no_cpu_fallback(monkeypatch):
     """Without the built library the binding raises instead of computing."""
     from paper_1409_4923_gb300 import engine as E
