@@ -10,12 +10,14 @@ def oracle_params(orc, prm):
     return orc.make_params(**d)
 
 
-def engine_run(E, torch, model, prm, seed, paths, dt, n_tr, n_avg, per_path=True, tuning=None):
-    """Run through the C ABI; returns (stats dict, per-path numpy dict or None)."""
+def engine_run(E, torch, model, prm, seed, paths, dt, n_tr, n_avg, per_path=True, tuning=None, ppt=1):
+    """Run through the C ABI; returns (stats dict, per-path numpy dict or None).
+    tuning: (threads per block, grid) or None; ppt: paths per lane."""
     eng = E.Engine(model, E.make_params(**prm), seed=seed)
     try:
         if tuning:
             eng.set_tuning(*tuning)
+        eng.set_paths_per_thread(ppt)
         out = None
         if per_path:
             out = {"X_f": torch.zeros(paths, dtype=torch.float64, device="cuda"),

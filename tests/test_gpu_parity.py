@@ -173,11 +173,19 @@ def test_ensemble_poisson_1024(E, W, orc):
 
 
 def test_ensemble_dichot_full_size(E, W, orc):
-    """The 2^20-path dichotomous workload at full size and horizon; the oracle
-    integrates a sample of 1024 of the same paths."""
+    """The 2^20-path dichotomous workload at full size and horizon, in the launch
+    shape the bench's autotuner picks (two paths per lane on packed FP32 pairs,
+    64-thread blocks, persistent grid); every per-path result equals that of one
+    path per lane bit for bit, and the oracle integrates a sample of 1024 of the
+    same paths."""
     s = W.run_spec("dichot_2p20")
     g_st, g = gc.engine_run(E, torch, s["model"], s["params"], s["seed"], s["paths"], s["dt"],
-                            s["n_transient"], s["n_avg"])
+                            s["n_transient"], s["n_avg"], tuning=(64, 0), ppt=2)
+    one_st, one = gc.engine_run(E, torch, s["model"], s["params"], s["seed"], s["paths"], s["dt"],
+                                s["n_transient"], s["n_avg"])
+    assert g_st["sums"] == one_st["sums"]
+    for k in g:
+        assert np.array_equal(g[k], one[k]), k
     assert g_st["n"] == s["paths"]
     sample = 1024
     first = s["paths"] - sample           # the last tiles of the launch
