@@ -24,6 +24,16 @@ def test_candidates_and_keys():
     assert AT.key("GB300", 0, 5, 1 << 20) != AT.key("GB300", 0, 6, 1 << 20)
     assert AT.key("GB300", 0, 5, 1 << 20) == AT.key("GB300", 0, 5, (1 << 20) + 5)
     assert all(s % 32 == 0 for s in AT.STEPS_PER_LAUNCH) and AT.STEPS_PER_LAUNCH[0] == 0
+    # a scan shape tuned on a few hundred items never serves a scan of 10^5 items
+    assert AT.scan_key("GB300", 0, 3, 288) != AT.scan_key("GB300", 0, 3, 294912)
+    assert AT.scan_key("GB300", 0, 3, 294912) == AT.scan_key("GB300", 0, 3, 300000)
+    assert AT.scan_key("GB300", 0, 3, 288) != AT.scan_key("GB300", 0, 5, 288)
+
+
+def test_tests_tune_into_a_private_cache():
+    import os
+    assert AT.cache_path() != AT.DEFAULT_CACHE
+    assert os.environ.get(AT.CACHE_ENV) == AT.cache_path()
 
 
 def test_cache_round_trip(tmp_path):
