@@ -12,9 +12,10 @@ Parity status per function (details in the pins under tests/):
                  amplitude law, dichotomous correlation and occupation)
   run_paths      pinned for the free, linear (OU), overdamped washboard
                  (Stratonovich), piecewise-linear (Eqs. 21-23) and inertial
-                 free/equipartition/driven-linear cases; the inertial driven
-                 washboard itself has no closed form: parity unpinned beyond
-                 those component pins.
+                 free/equipartition/driven-linear cases, and for the inertial
+                 driven washboard with the noise off (second-order convergence
+                 to SciPy's DOP853); with noise that model has no closed form:
+                 parity unpinned beyond those pins.
 """
 import ctypes
 import os

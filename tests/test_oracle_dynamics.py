@@ -121,6 +121,36 @@ def test_inertial_driven_linear_deterministic(orc):
         assert all(1.8 < x < 2.2 for x in s), (ev, ex)
 
 
+def test_inertial_driven_washboard_deterministic(orc):
+    """The bench's nonlinear model with the noise off, x'' = -g x' - 2 pi V0
+    cos(2 pi x) + a cos(w t) + F (washboard V0 sin(2 pi x), drive and bias),
+    over one drive period from fixed (x0, v0): the scheme converges at second
+    order to SciPy's DOP853 solution at 1e-13 tolerances.  This pins the
+    washboard force's sign, factor and argument together with the drive and the
+    damping of the model the engine is timed on (the linear tests above cover
+    the drive alone).  One period keeps the chaotic growth of trajectory
+    differences out of the comparison."""
+    solve_ivp = pytest.importorskip("scipy.integrate").solve_ivp
+    g, a, w, F, V0, x0, v0 = 0.9, 4.2, 4.9, 0.1, 1.0, 0.3, 0.7
+    T = 2 * math.pi / w
+
+    def rhs(t, y):
+        return [y[1], -g * y[1] - 2 * math.pi * V0 * math.cos(2 * math.pi * y[0]) + a * math.cos(w * t) + F]
+
+    ref = solve_ivp(rhs, (0.0, T), [x0, v0], method="DOP853", rtol=1e-13, atol=1e-13).y[:, -1]
+    ex, ev = [], []
+    for n in (200, 400, 800):
+        p = orc.make_params(gamma=g, a=a, omega=w, F=F, V0=V0, x0_lo=x0, x0_hi=x0, v0_lo=v0, v0_hi=v0)
+        r = orc.run_paths(orc.INERTIAL_WASHBOARD, p, 0, 0, 1, T / n, 0, n)
+        ex.append(abs(r["X_f"][0] - ref[0]))
+        ev.append(abs(r["v_f"][0] - ref[1]))
+    assert ex[-1] < 5e-6 and ev[-1] < 1e-5, (ex, ev)
+    sx = [math.log2(ex[i] / ex[i + 1]) for i in range(2)]
+    sv = [math.log2(ev[i] / ev[i + 1]) for i in range(2)]
+    assert all(1.9 < x < 2.1 for x in sx), sx
+    assert all(1.9 < x < 2.7 for x in sv), sv          # v approaches order 2 from above
+
+
 def test_overdamped_driven_deterministic(orc):
     """Noise-free x' = a cos(w t) + F: x(T) = F T + (a / w) sin(w T) to O(dt^2)."""
     a, w, F, T = 1.3, 2.0, 0.7, 3.0
