@@ -848,10 +848,11 @@ int sde_mlp_fit(sde_mlp* n, const float* X, const float* T, uint64_t N, uint64_t
                 float lr, float lr_final, float beta1, float beta2, float eps, uint64_t seed, float* losses)
 {
     if (!n) return SDE_EINVAL;
-    if (!X || !T || N == 0 || N > (1ull << 30) || steps == 0 || steps > (1ull << 26) || batch == 0 ||
+    // the schedule table takes 12 bytes per step on the host and the device
+    if (!X || !T || N == 0 || N > (1ull << 30) || steps == 0 || steps > (1ull << 22) || batch == 0 ||
         batch > kMaxBatch || batch > N)
         return mfail(n, SDE_EINVAL,
-                     "bad fit arguments (1 <= batch <= min(N, 65536), N <= 2^30, 1 <= steps <= 2^26)");
+                     "bad fit arguments (1 <= batch <= min(N, 65536), N <= 2^30, 1 <= steps <= 2^22)");
     if (!(lr > 0.0f) || !(lr_final > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
         !(eps > 0.0f))
         return mfail(n, SDE_EINVAL, "bad Adam hyper-parameters");
