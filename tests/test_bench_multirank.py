@@ -1,6 +1,7 @@
-"""The N > 1 timing path of bench.py on two gloo ranks (CPU): the slowest
+"""bench.py on the CPU: the N > 1 timing path on two gloo ranks (the slowest
 rank's time is what every rank reports, and the weak-scaling value counts all
-ranks' work over that time."""
+ranks' work over that time), and the JSON line of the reference arm (the FP64
+oracle on the host cores)."""
 import os
 import socket
 
@@ -51,3 +52,22 @@ def test_single_process_passthrough():
     import bench
     assert bench.reduce_max_over_ranks(3.25) == 3.25
     assert bench.weak_scaling_value(10, 1, 2, 4.0) == 5.0
+
+
+def test_reference_arm_json_line():
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["unit"] == "path-steps/s" and line["value"] > 0
+    assert line["config"]["workload"] == "dichot_2p20" and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
