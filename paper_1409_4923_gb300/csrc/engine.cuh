@@ -652,7 +652,8 @@ __device__ __forceinline__ void advance_path(PathState& S, const PointConsts& P,
 
 // The same integration for PPT paths per lane, interleaved step by step so
 // that their independent dependency chains fill each other's latencies; the
-// drive values and the loop are shared.  Every path takes exactly the
+// drive values and the loop are shared.  Two inertial paths run their chunks
+// on packed FP32 pairs (chunk_steps_x2).  Every path takes exactly the
 // operations of run_steps (a chunk whose Poisson events do not fit the queue
 // of some path takes all paths' events inline, which gives the same values),
 // so results do not depend on PPT.
