@@ -85,7 +85,9 @@ int sde_mlp_train_step(sde_mlp* net, const float* x, const float* t, uint64_t M,
  * the work already on the network's stream; returns when the steps are done.
  * Requires 1 <= batch <= min(N, 65536), N <= 2^30, 1 <= steps <= 2^22 (else
  * SDE_EINVAL); the step schedule takes 12 bytes per step on the host and the
- * device for the duration of the call. */
+ * device for the duration of the call.  No other call may use the same
+ * network meanwhile (the capture runs the network's kernels on the private
+ * stream). */
 int sde_mlp_fit(sde_mlp* net, const float* X, const float* T, uint64_t N, uint64_t steps,
                 uint32_t batch, float lr, float lr_final, float beta1, float beta2, float eps,
                 uint64_t seed, float* losses);
