@@ -6,11 +6,44 @@ the comparison is with a continuum result, an allowance for the scheme's
 discretisation error (stated at each check).
 """
 import math
+import os
 
 import numpy as np
 import pytest
 
 import closed_forms as cf
+
+
+def _paper_settings():
+    """The validation settings the paper states for Models I and II (Sec. 6 and
+    the Fig. 3 caption), from tests/golden/paper_validation_settings.txt:
+    {model: {key: value or list of values}}."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_validation_settings.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, *items = line.split()
+            d = {}
+            for item in items:
+                k, v = item.split("=")
+                vals = [float(x) for x in v.split(",")]
+                d[k] = vals if len(vals) > 1 else vals[0]
+            out[name] = d
+    return out
+
+
+PAPER = _paper_settings()
+
+
+def test_paper_settings_fixture():
+    assert PAPER["model_I"]["a"] == [1.5, 2.5] and PAPER["model_I"]["spp"] == 400
+    assert PAPER["model_II"]["Fa"] == 3 and PAPER["model_II"]["Fb"] == [1.1, 1.6]
+    assert PAPER["model_II"]["spp"] == 200
+    assert PAPER["model_I"]["DG"] == 0 and PAPER["model_II"]["DG"] == 0
+    assert PAPER["model_I"]["transient_fraction"] == PAPER["model_II"]["transient_fraction"] == 0.1
 
 
 def _var_se(x):
@@ -267,38 +300,42 @@ def test_stratonovich_tilted_washboard(orc, V0, F, D):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("a,DP", [(1.5, 1.0), (2.5, 2.0)])
+@pytest.mark.parametrize("a,DP", list(zip(PAPER["model_I"]["a"], (1.0, 2.0))))
 def test_model_I_eq21a(orc, a, DP):
     """Model I (Eq. 1), D_G = 0, L = 2: <v> = 2 J_I (Eqs. 21a-23), settings of the
     paper's validation (spp = 400, dt = (1/lambda)/400, 10 % transient dropped).
     The compensated bias makes the kick process exactly zero-mean; the residual
     discretisation allowance is 0.003."""
+    cfg = PAPER["model_I"]
     lam, zeta = a * a / DP, DP / a
-    dt = (1 / lam) / 400
-    n = int(200 / lam / dt)
+    dt = (1 / lam) / cfg["spp"]
+    n = int(200 / lam / dt)                       # 200 mean kick intervals (the paper: 1000)
+    n_tr = int(round(n * cfg["transient_fraction"]))
     p = orc.make_params(**{"lambda": lam}, zeta=zeta, x0_lo=-1.0, x0_hi=1.0,
                         noise=orc.POISSON | orc.POIS_COMPENSATED)
-    r = orc.run_paths(orc.OVERDAMPED_PWL, p, 0, 0, 2048, dt, n // 10, n - n // 10)
-    s = orc.stats(r, n - n // 10)
+    r = orc.run_paths(orc.OVERDAMPED_PWL, p, 0, 0, 2048, dt, n_tr, n - n_tr)
+    s = orc.stats(r, n - n_tr)
     want = cf.eq21a_velocity(a, DP)
     assert abs(s["mean_v"] - want) < 4 * s["stderr_v"] + 0.003, (s, want)
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("Fb,tau", [(1.1, 1.0), (1.6, 0.5)])
+@pytest.mark.parametrize("Fb,tau", list(zip(PAPER["model_II"]["Fb"], (1.0, 0.5))))
 def test_model_II_eq21b_corrected_sign(orc, Fb, tau):
     """Model II (Eq. 12), D_G = 0, F_a = 3 (the paper's validation values), zero
     mean (F_a mu_b = F_b mu_a).  Matches Eq. 21b with (beta_- - beta_+) and
     rejects the printed sign."""
-    Fa = 3.0
+    cfg = PAPER["model_II"]
+    Fa = cfg["Fa"]
     mua, mub = Fa / (tau * (Fa + Fb)), Fb / (tau * (Fa + Fb))
     ref = min(1 / mua, 1 / mub)
-    dt = ref / 200
-    n = int(400 * ref / dt)
+    dt = ref / cfg["spp"]
+    n = int(400 * ref / dt)                       # 400 x min(tau_a, tau_b) (the paper: 1000)
+    n_tr = int(round(n * cfg["transient_fraction"]))
     p = orc.make_params(Fa=Fa, Fb=Fb, mua=mua, mub=mub, x0_lo=-1.0, x0_hi=1.0,
                         noise=orc.DICHOT)
-    r = orc.run_paths(orc.OVERDAMPED_PWL, p, 0, 0, 2048, dt, n // 10, n - n // 10)
-    s = orc.stats(r, n - n // 10)
+    r = orc.run_paths(orc.OVERDAMPED_PWL, p, 0, 0, 2048, dt, n_tr, n - n_tr)
+    s = orc.stats(r, n - n_tr)
     want = cf.eq21b_velocity(Fa, Fb, tau)
     printed = cf.eq21b_velocity(Fa, Fb, tau, printed_sign=True)
     assert abs(s["mean_v"] - want) < 4 * s["stderr_v"] + 0.005, (s, want)
