@@ -121,7 +121,9 @@ typedef struct sde_ctx sde_ctx;
 int sde_create(sde_ctx** out, sde_model model, const sde_params* p, uint64_t seed,
                void* cuda_stream);
 
-/* Replace the parameters of an existing context (validated, copied). */
+/* Replace the parameters of an existing context (validated, copied);
+ * parameter meaning as in sde_create.  A convenience for scans driven from
+ * the host: no passage of the paper defines this call. */
 int sde_set_params(sde_ctx* ctx, const sde_params* p);
 
 /* Enqueue one Monte Carlo run on the context's stream: `paths` independent
@@ -238,19 +240,24 @@ int sde_local_error(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_steps, d
 
 /* Reduce `n` device doubles `vals` to {n, sum, sum of squares} with the same
  * FP64 fold the engine uses (pairwise within a warp, Kahan across items).
- * `out3` is a host array of three doubles.  Synchronises the stream. */
+ * `out3` is a host array of three doubles.  Synchronises the stream.
+ * Test aid: it exposes the reduction step of Eq. 31's ensemble average so
+ * that it can be checked on its own; the paper has no such call. */
 int sde_reduce_f64(sde_ctx* ctx, const double* vals, uint64_t n, double* out3);
 
 /* Words of the engine's device Philox4x32-10 for counters ctr[4*i..4*i+3]
  * (host array) and key (seed): writes 4*n words to the host array `out`.
- * Runs on the device; exposed so the stream contract can be tested. */
+ * Runs on the device.  Test aid, exposed so that the stream contract can be
+ * checked bit for bit; the paper has no such call (it uses cuRAND). */
 int sde_philox_words(sde_ctx* ctx, const uint32_t* ctr, uint64_t n, uint64_t seed,
                      uint32_t* out);
 
 /* Launch shape of the path kernels of this context: threads per block
  * (32..128, multiple of 32) and blocks in the grid (0 = one persistent wave
  * from the occupancy calculator).  Results never depend on the shape; the
- * autotuner of the Python layer picks it.  EINVAL outside those ranges. */
+ * autotuner of the Python layer picks it.  EINVAL outside those ranges.
+ * Tuning aid: the paper fixes no launch shape (Sec. 5 only asks for enough
+ * threads per block to keep the GPU busy). */
 int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
 
 /* Paths integrated by one GPU lane (1 or 2; default 1).  With 2, each lane
@@ -258,7 +265,9 @@ int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
  * dependency chains hide each other's latencies and the drive values and
  * loop work are shared; each path takes exactly the operations it takes with
  * 1, so results do not change.  Applies to sde_run, sde_run_paths and the
- * per-point launches of sde_scan for the overdamped models.  EINVAL otherwise. */
+ * per-point launches of sde_scan for the overdamped models.  EINVAL otherwise.
+ * Tuning aid with no counterpart in the paper, which runs one path per
+ * thread (Algorithm 5). */
 int sde_set_paths_per_thread(sde_ctx* ctx, int paths_per_thread);
 
 /* Steps per kernel launch of sde_run / sde_run_paths (Algorithm 5's
@@ -272,7 +281,7 @@ int sde_set_steps_per_launch(sde_ctx* ctx, uint64_t steps);
 
 /* Resident blocks per SM of this context's path kernel at `block_threads`
  * (and the context's paths per thread), and the device's SM count (host
- * outputs). */
+ * outputs).  Tuning aid for the autotuner; the paper has no such call. */
 int sde_occupancy(sde_ctx* ctx, int block_threads, int* blocks_per_sm, int* sm_count);
 
 /* Largest path count of sde_run_noalloc. */
@@ -294,14 +303,17 @@ int sde_occupancy(sde_ctx* ctx, int block_threads, int* blocks_per_sm, int* sm_c
  *     sums as sde_stats_t.sums (paths, sum vbar, sum vbar^2, sum v, sum v^2);
  *   status_out: caller-owned DEVICE int32 (or NULL) that receives SDE_OK.
  * Scratch (the work counter, the status word and 5 doubles per 32 paths,
- * 2.6 MB in all) is one file-scope device array of fixed size, held by every
- * GPU that loads this library until the process exits.  All calls share it
- * and it keeps the last call's contents (each call clears what must start at
- * zero), so calls whose work overlaps on the GPU (other streams, other host
- * threads on the same device) race: serialise them.  The first call on each
- * device looks the array's device address up (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Errors: SDE_EINVAL, SDE_ECUDA;
- * the message is sde_last_error(NULL). */
+ * 2.6 MB in all) is one file-scope device array of fixed size.  CUDA loads
+ * the library's device code on a device lazily, so the array comes into being
+ * on a device at the first call there (the driver then reserves it, once) and
+ * stays until the process exits.  That first call on each device also looks
+ * the array's device address up (cudaGetSymbolAddress): make it at start-up,
+ * before any memory arena takes over the device and before any stream
+ * capture; later calls allocate nothing.  All calls share the array and it
+ * keeps the last call's contents (each call clears what must start at zero),
+ * so calls whose work overlaps on the GPU (other streams, other host threads
+ * on the same device) race: serialise them.  Errors: SDE_EINVAL, SDE_ECUDA;
+ * the message is sde_last_error(NULL) in the calling thread. */
 int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t seed, uint64_t paths,
                     double dt, uint64_t n_transient, uint64_t n_avg, void* cuda_stream,
                     double* out5, int32_t* status_out);
@@ -309,11 +321,13 @@ int sde_run_noalloc(sde_model model, const sde_params* p, uint64_t seed, uint64_
 /* Free everything the context owns (waits for its stream first). */
 void sde_destroy(sde_ctx* ctx);
 
-/* Message of the last error on `ctx` (or of the last failed sde_create when
- * ctx is NULL).  Valid until the next call on the same context. */
+/* Message of the last error on `ctx`, or, when ctx is NULL, of the last
+ * failed call without a context (sde_create, sde_run_noalloc) made by the
+ * calling host thread (each thread has its own).  Valid until the next call on
+ * the same context (or, for NULL, the next such call in the thread). */
 const char* sde_last_error(const sde_ctx* ctx);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper). */
 const char* sde_version(void);
 
 #ifdef __cplusplus

@@ -124,7 +124,9 @@ struct sde_ctx {
     size_t state_bytes = 0;
 };
 
-static std::string g_create_error;
+// Message of the last failed call made without a context (sde_create,
+// sde_run_noalloc): one per host thread, so that threads do not race on it.
+static thread_local std::string g_create_error;
 
 int fail(sde_ctx* c, int code, const std::string& msg)
 {

@@ -12,7 +12,7 @@
 // writes and reads 512 bytes of h2 and writes 8 bytes of outputs, instead of
 // the four layers' 3 KB.
 //
-// One persistent CTA of 256 threads per SM.  It copies its 256 x 256 layer's
+// One persistent CTA of 512 threads (16 warps) per SM.  It copies its 256 x 256 layer's
 // weights W (BF16, 128 KB) into shared memory once, in the 128-byte-swizzled
 // K-major layout the tensor core reads.  Per tile, the A operand is staged in
 // the same layout (64 KB) and one elected thread issues the 16 MMAs of K = 256

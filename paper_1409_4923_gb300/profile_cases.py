@@ -6,7 +6,7 @@
   python -m paper_1409_4923_gb300.profile_cases fit --rows 16384 --steps 200
 
 Each case runs its launch twice (a warm-up and the one to capture) and
-prints a checksum, so `ncu -s 1 -c 1 -k <kernel>` captures a warm launch.
+prints a checksum, so `ncu --clock-control none -s 1 -c 1 -k <kernel>` captures a warm launch.
 """
 import argparse
 import sys

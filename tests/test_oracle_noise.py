@@ -130,3 +130,31 @@ def test_three_point_steps_sharing_a_word_are_independent(orc):
             chi2 = ((obs - exp) ** 2 / exp).sum()
             assert chi2 < 26.1, (lag, k, chi2)   # 8 dof, p = 0.001
     assert abs(np.abs(x[x != 0]).mean() - c) < 1e-15
+
+
+def test_three_point_four_steps_of_one_word_jointly_independent(orc):
+    """All 81 joint outcomes of the four steps that share one Philox word
+    (uniforms r, 6r, 36r, 216r mod 2^32; Algorithm 2 draws a fresh uniform per
+    step) against the product law of Eq. 25's three-point distribution,
+    (1/6, 1/6, 2/3)^4: a chi-square test with 80 degrees of freedom, which sees
+    any dependence among the four digits of one word, not only pairwise lags."""
+    Q, dt = 0.5, 0.01
+    p = orc.make_params(Q=Q, noise=orc.GAUSS)
+    x = _seq(orc, 1, orc.OVERDAMPED_WASHBOARD, p, 17, 64, dt, 16000)
+    cls = np.where(x < 0, 0, np.where(x > 0, 1, 2))
+    words = cls.reshape(cls.shape[0], -1, 4).reshape(-1, 4)        # steps 4i .. 4i + 3
+    cell = ((words[:, 0] * 3 + words[:, 1]) * 3 + words[:, 2]) * 3 + words[:, 3]
+    obs = np.bincount(cell, minlength=81).astype(np.float64)
+    probs = np.array([1 / 6, 1 / 6, 2 / 3])
+    exp = np.einsum("i,j,k,l->ijkl", probs, probs, probs, probs).ravel() * len(cell)
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    assert chi2 < sst.chi2.ppf(0.999, 80), chi2
+    # and the test has power: 10 % of the words with their last digit copied
+    # from the first (a dependence a pairwise lag-3 test would also see, here
+    # one of 81 cells) is rejected
+    bad = words.copy()
+    sel = np.arange(len(bad)) % 10 == 0
+    bad[sel, 3] = bad[sel, 0]
+    cb = ((bad[:, 0] * 3 + bad[:, 1]) * 3 + bad[:, 2]) * 3 + bad[:, 3]
+    ob = np.bincount(cb, minlength=81).astype(np.float64)
+    assert ((ob - exp) ** 2 / exp).sum() > sst.chi2.ppf(0.999, 80)
