@@ -157,6 +157,9 @@ typedef struct {
  * `npts` points (host array, copied) run in one persistent launch over
  * (point, 32-path tile) work items ordered longest first, replayed from a
  * CUDA graph when the shape repeats, and folded per point in a fixed order.
+ * For the inertial model without Poisson noise an item is 64 paths of one
+ * point (two paths per GPU lane on packed FP32 pairs); each 32-path tile still
+ * writes its own partial sums, so a point's result equals its single run.
  * All points share the context's model; each point's noise_flags must equal
  * those of the first point.  Writes npts statistics to the host array `out`
  * (synchronises the stream).  deadline_ms > 0 bounds the device time: work

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["point_inertial.cu", "point_overdamped_washboard.cu", "point_overdamped_pwl.cu",
          "point_inertial_x2.cu", "point_overdamped_washboard_x2.cu", "point_overdamped_pwl_x2.cu",
          "segment_m0.cu", "segment_m1.cu", "segment_m2.cu", "chi_m0.cu", "chi_m1.cu", "chi_m2.cu",
-         "aux_kernels.cu", "capi.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu"]
+         "aux_kernels.cu", "scan_x2.cu", "capi.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu"]
 
 
 def nvcc():

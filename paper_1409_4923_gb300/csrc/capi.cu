@@ -39,6 +39,7 @@ struct PendingScan {
     uint32_t flags = 0;
     uint32_t total_items = 0;
     bool scan_kernel = false;
+    bool x2 = false;              // two paths per lane (64-path items)
     size_t off_counters = 0, off_out5 = 0, off_ranges = 0, off_partials = 0, off_pts = 0,
            off_items = 0;
     std::vector<uint64_t> n_avg;
@@ -551,26 +552,33 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
     std::vector<uint32_t> order(npts);
     for (uint32_t i = 0; i < npts; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return steps[a] > steps[b]; });
+    const bool use_scan_kernel = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
+    // Without Poisson noise the scan kernel takes two paths per lane: a work
+    // item is 64 paths of one point and writes the partial records of its two
+    // 32-path tiles, so each point's records start at an even index (a point
+    // with an odd tile count leaves one record unused and unfolded).
+    const bool x2 = use_scan_kernel && !(flags & SDE_NOISE_POISSON);
+    const uint64_t item_paths = x2 ? 64ull : 32ull;
     std::vector<uint2> ranges(npts), items;
     uint64_t total_items = 0;
-    for (uint32_t i = 0; i < npts; ++i) total_items += (pts[i].paths + 31ull) / 32ull;
-    if (total_items > 0xFFFFFF00ull) return fail(c, SDE_EINVAL, "too many work items");
+    for (uint32_t i = 0; i < npts; ++i) total_items += (pts[i].paths + item_paths - 1) / item_paths;
+    if (total_items > 0x7FFFFF00ull) return fail(c, SDE_EINVAL, "too many work items");
+    const uint64_t records = x2 ? 2 * total_items : total_items;
     items.reserve(total_items);
     for (uint32_t k = 0; k < npts; ++k) {
         const uint32_t i = order[k];
-        const uint32_t first = (uint32_t)items.size();
-        const uint64_t ni = (pts[i].paths + 31ull) / 32ull;
-        for (uint64_t t = 0; t < ni; ++t) items.push_back(make_uint2(i, (uint32_t)(32ull * t)));
-        ranges[i] = make_uint2(first, (uint32_t)ni);
+        const uint32_t first = (uint32_t)(x2 ? 2 * items.size() : items.size());
+        const uint64_t ni = (pts[i].paths + item_paths - 1) / item_paths;
+        for (uint64_t t = 0; t < ni; ++t) items.push_back(make_uint2(i, (uint32_t)(item_paths * t)));
+        ranges[i] = make_uint2(first, (uint32_t)((pts[i].paths + 31ull) / 32ull));
         int rc = make_point(c, c->model, pts[i].p, pts[i].dt, pts[i].paths, pts[i].n_transient,
                             pts[i].n_avg, P[i]);
         if (rc) return rc;
     }
-    const bool use_scan_kernel = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
     const size_t off_items = align256(sizeof(PointConsts) * npts);
     const size_t off_counters = off_items + align256(sizeof(uint2) * total_items);
     const size_t extra = off_counters + align256(sizeof(uint32_t) * npts);
-    const Layout L = layout(npts, total_items, extra);
+    const Layout L = layout(npts, records, extra);
     int rc;
     if ((rc = ensure_ws(c, L.total))) return rc;
     const size_t host_need = sizeof(double) * 5 * npts + 64;
@@ -598,7 +606,11 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
             bool capture = c->stream != nullptr;
             if (capture) SDE_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaMemsetAsync(base, 0, 8, c->stream);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && x2)
+                e = launch_scan_x2(dich_kind(flags), (flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0, d_pts,
+                                   d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count,
+                                   c->stream);
+            else if (e == cudaSuccess)
                 e = launch_scan((flags & SDE_NOISE_POISSON) != 0, dich_kind(flags),
                                 (flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0, d_pts,
                                 d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream);
@@ -652,6 +664,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
     S.flags = flags;
     S.total_items = (uint32_t)total_items;
     S.scan_kernel = use_scan_kernel;
+    S.x2 = x2;
     S.off_counters = L.off_extra + off_counters;
     S.off_out5 = L.off_out5;
     S.off_ranges = L.off_ranges;
@@ -690,10 +703,16 @@ int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)
     SDE_CUDA(c, cudaMemsetAsync(ws.status, 0, 4, c->stream));
     if (S.scan_kernel) {
         const LaunchConsts K = make_launch(c->seed, S.total_items, budget);
-        SDE_CUDA(c, launch_scan((S.flags & SDE_NOISE_POISSON) != 0, dich_kind(S.flags),
-                                (S.flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0,
-                                (const PointConsts*)(base + S.off_pts), (const uint2*)(base + S.off_items),
-                                K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
+        if (S.x2)
+            SDE_CUDA(c, launch_scan_x2(dich_kind(S.flags), (S.flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0,
+                                       (const PointConsts*)(base + S.off_pts),
+                                       (const uint2*)(base + S.off_items), K, ws, c->block_threads,
+                                       c->grid_blocks, c->sm_count, c->stream));
+        else
+            SDE_CUDA(c, launch_scan((S.flags & SDE_NOISE_POISSON) != 0, dich_kind(S.flags),
+                                    (S.flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0,
+                                    (const PointConsts*)(base + S.off_pts), (const uint2*)(base + S.off_items),
+                                    K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
     } else {
         uint32_t* d_counters = (uint32_t*)(base + S.off_counters);
         for (uint32_t i = 0; i < S.npts; ++i) {

@@ -51,6 +51,13 @@ cudaError_t launch_scan(bool pois, int dich, int gauss, const PointConsts* pts_d
                         const LaunchConsts& K, const Workspace& ws, int block_threads,
                         int grid_blocks, int sm_count, cudaStream_t st);
 
+// The same scan without Poisson noise, two paths per lane: item k is 64 paths
+// (point, first path) and writes the partial records 2k and 2k + 1 of its two
+// 32-path tiles.
+cudaError_t launch_scan_x2(int dich, int gauss, const PointConsts* pts_dev, const uint2* items_dev,
+                           const LaunchConsts& K, const Workspace& ws, int block_threads,
+                           int grid_blocks, int sm_count, cudaStream_t st);
+
 // Fixed-order FP64 fold of item partials: ranges[p] = (first item, item count),
 // out5[5 p .. 5 p + 4] receives the point's five sums.
 cudaError_t launch_fold(const double* partials, const uint2* ranges, uint32_t npts,

@@ -15,6 +15,11 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t t0 = K.budget_ns ? globaltimer_ns() : 0ull;
+    uint32_t* win = nullptr;
+    if constexpr (WindowedFlips<MODEL, POIS, DICH, GAUSS, PPT>::value) {
+        extern __shared__ uint32_t sde_point_smem[];
+        win = sde_point_smem + (threadIdx.x >> 5) * kWinWordsPerWarp;
+    }
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, t0, (uint32_t)PPT);
         if (item == 0xffffffffu) break;
@@ -30,7 +35,7 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
 #pragma unroll
             for (int p = 0; p < PPT; ++p) path[p] = (item + (uint32_t)p) * 32u + lane;
             PathResult R[PPT];
-            simulate_paths<MODEL, POIS, DICH, GAUSS, PPT>(P, K, path, lane, R);
+            simulate_paths<MODEL, POIS, DICH, GAUSS, PPT>(P, K, path, lane, R, win);
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
                 if (item + (uint32_t)p >= K.n_items) break;      // past the last item: no output
@@ -76,15 +81,24 @@ constexpr auto point_kernel_for()
     else return point_kernel<MODEL, POIS, DICH, GAUSS, PPT>;
 }
 
+// Dynamic shared memory of a launch: the flip windows of its warps.
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
+constexpr size_t point_smem_bytes(int block_threads)
+{
+    return WindowedFlips<MODEL, POIS, DICH, GAUSS, PPT>::value
+               ? (size_t)(block_threads / 32) * kWinWordsPerWarp * sizeof(uint32_t) : 0u;
+}
+
 template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Workspace& ws,
                            const PathOutPtrs& po, int block_threads, int grid_blocks,
                            int sm_count, cudaStream_t st)
 {
     auto kern = point_kernel_for<MODEL, POIS, DICH, GAUSS, PPT>();
+    const size_t smem = point_smem_bytes<MODEL, POIS, DICH, GAUSS, PPT>(block_threads);
     if (grid_blocks <= 0) {
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_threads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_threads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         const uint64_t warps = ((uint64_t)K.n_items + PPT - 1) / PPT;
@@ -93,7 +107,7 @@ cudaError_t launch_point_t(const PointConsts& P, const LaunchConsts& K, const Wo
         grid_blocks = (int)(need < cap ? need : cap);
         if (grid_blocks < 1) grid_blocks = 1;
     }
-    kern<<<grid_blocks, block_threads, 0, st>>>(P, K, ws.counter, ws.status, ws.partials, po);
+    kern<<<grid_blocks, block_threads, smem, st>>>(P, K, ws.counter, ws.status, ws.partials, po);
     return cudaGetLastError();
 }
 
@@ -102,7 +116,8 @@ int blocks_per_sm_t(int block_threads)
 {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, point_kernel_for<MODEL, POIS, DICH, GAUSS, PPT>(),
-                                                  block_threads, 0);
+                                                  block_threads,
+                                                  point_smem_bytes<MODEL, POIS, DICH, GAUSS, PPT>(block_threads));
     return per_sm;
 }
 
