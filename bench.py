@@ -271,10 +271,69 @@ def run_engine(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)
     eng.close()
+    if world == 1 and args.scan_valid > 0:
+        line["scan"] = scan_record(args.scan_valid, local)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def scan_record(n_valid, device_index):
+    """The metric's second half, measured after the timed path-steps region:
+    points per second at |d<v>| <= 0.01 of the surrogate-guided 1024 x 1024
+    dichotomous scan against plain Monte Carlo on the same grid, and the
+    64 x 64 Poissonian batched scan (one persistent launch).
+
+    Plain Monte Carlo is measured, not assumed: n_valid random grid points run
+    through the same batched scan at the plain map's 8192 paths (their values
+    are the plain map's values there, bit for bit), which gives both the
+    plain method's points/s and the guided map's error on those points.  The
+    plain map's full cost is extrapolated from that rate:
+    t_plain_map = grid points / (n_valid / t_valid)."""
+    from paper_1409_4923_gb300 import guided, timing
+    with ClockSampler(device_index) as clk:
+        g = guided.guided_dichot_scan(n_valid=n_valid, log=lambda *a: None)
+        s64 = timing.time_scan("scan_64x64", reps=2)
+    npts = g["grid"][0] * g["grid"][1]
+    t = g["seconds"]
+    plain_pps = g["points_per_s_plain"]
+    return {
+        "guided_1024x1024": {
+            "workload": "dichotomous <v>(F, b) on a 1024 x 1024 grid, 200 + 2000 periods, spp 200; "
+                        "plain map at 8192 paths per point",
+            "seconds": {k: round(v, 3) for k, v in t.items()},
+            "points_per_s": g["points_per_s_guided"],
+            "labels": {"points": g["label_points"], "paths": g["label_paths"],
+                       "path_steps": g["path_steps_labels"]},
+            "train": {"networks": 2, "adam_steps": g["train_steps"],
+                      "heldout_rmse": g["calibration"]["rmse"],
+                      "kappa": g["calibration"]["kappa"]},
+            "flagged": g["flagged"], "flagged_fraction": g["flagged_fraction"],
+            "path_steps_reruns": g["path_steps_reruns"],
+            "path_steps_guided_total": g["path_steps_reruns"] + g["path_steps_labels"],
+            "path_steps_plain_map": g["path_steps_plain_map"],
+            "ratio_path_steps_plain_over_guided": g["ratio_plain_over_guided_total"],
+            "validation": {"points": g["validation_points"], "paths": g["rerun_paths"],
+                           "max_abs_err": g["validation_max_abs_err"],
+                           "rms_err": g["validation_rms_err"],
+                           "frac_within_0.01": g["validation_frac_within_0.01"],
+                           "plain_stderr_median": g["plain_mc_stderr_median"]},
+        },
+        "plain_mc": {
+            "points_per_s": plain_pps,
+            "path_steps_per_s": g["validation_points"] * g["rerun_paths"] * g["path_len"] / t["plain_validation"],
+            "seconds_full_map_extrapolated": npts / plain_pps,
+            "formula": "grid points / (validation points / validation seconds)",
+        },
+        "guided_over_plain_points_per_s": g["points_per_s_guided"] / plain_pps,
+        "scan_64x64": {"workload": "4096 Poisson points, 64 x 64 grid of F x log Q, paths 256..16384, "
+                                   "500..3000 averaged periods, one persistent graph-replayed launch",
+                       "seconds": s64["seconds"], "points_per_s": s64["points_per_s"],
+                       "path_steps_per_s": s64["path_steps_per_s"],
+                       "launch_shape": s64["launch_shape"]},
+        "clocks": clk.summary(),
+    }
 
 
 def _oracle_sample(spec, paths, threads=None):
@@ -348,6 +407,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default launch knobs instead of the autotuner's")
+    ap.add_argument("--scan-valid", type=int, default=65536,
+                    help="grid points of the plain-MC validation of the guided scan record "
+                         "(0: no scan record; single GPU only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

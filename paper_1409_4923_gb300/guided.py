@@ -251,6 +251,8 @@ def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=4096, rerun_
     cost_rerun = float(len(idx)) * rerun_paths * g.path_len
     return {
         "grid": [nx, ny], "flagged": int(nflag), "flagged_fraction": nflag / float(nx * ny),
+        "label_points": int(n_label + n_hold), "label_paths": int(label_paths),
+        "rerun_paths": int(rerun_paths), "path_len": int(g.path_len), "train_steps": int(steps),
         "validation_points": int(len(vidx)), "validation_max_abs_err": float(err.max()),
         "validation_frac_within_0.01": float(np.mean(err <= 0.01)),
         "validation_rms_err": float(np.sqrt(np.mean(err ** 2))),
