@@ -10,9 +10,11 @@ with dichotomous + Gaussian noise, dt = (2 pi / 4.9) / 200, 200 + 2000 periods
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
-With N > 1 (torchrun) every rank runs its own 2^20 paths under its own seed
-(independent shards, no collective on the data path); value = all ranks'
-path-steps / the slowest rank's time.
+With N > 1 (torchrun) rank r runs paths [r 2^20, (r + 1) 2^20) of one
+ensemble under one seed (weak scaling), and the ranks' five FP64 sums are
+added (one 40-byte all-reduce per step, the only exchange Eq. 31 needs), so
+the result is <v> over N 2^20 paths; value = all ranks' path-steps / the
+slowest rank's time.
 """
 import argparse
 import json
@@ -152,6 +154,37 @@ def weak_scaling_value(units_per_rank, world, steps, t_max):
     return float(units_per_rank) * world * steps / t_max
 
 
+def shard_range(paths_per_rank, rank):
+    """Paths of rank r under weak scaling: [r P, (r + 1) P) of one ensemble
+    (one seed; the path index selects the random counters), so N ranks
+    integrate the first N P realisations of the same ensemble."""
+    return rank * paths_per_rank, paths_per_rank
+
+
+def combine_sums(sums5, device=None):
+    """Eq. 31's only exchange between path ranges: the sum over ranks of the
+    five FP64 sums (paths, sum vbar, sum vbar^2, sum v, sum v^2).  Without a
+    process group the sums are returned as they are."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in sums5]
+    t = torch.tensor([float(x) for x in sums5], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def ensemble_stats(s5, n_avg):
+    """Mean, variance and standard error of Eq. 31's quotient and the time moments of v
+    from the five sums (as sde_stats computes them)."""
+    n = s5[0]
+    mean = s5[1] / n
+    var = max(0.0, (s5[2] - n * mean * mean) / (n - 1.0)) if n > 1 else 0.0
+    tmean = s5[3] / (n * n_avg)
+    return {"n": int(n), "mean_v": mean, "var_v": var, "stderr_v": math.sqrt(var / n),
+            "tmean_v": tmean, "tvar_v": s5[4] / (n * n_avg) - tmean * tmean}
+
+
 def run_engine(args):
     import torch
     import torch.distributed as dist
@@ -171,14 +204,15 @@ def run_engine(args):
     knobs = dict(autotune.DEFAULT)
     if not args.no_autotune:
         t = autotune.tune(spec["model"], prm, dt, paths, n_probe_steps=2048,
-                          seed=spec["seed"] + rank, stream=stream)
+                          seed=spec["seed"], stream=stream)
         knobs = {f: t[f] for f in autotune.DEFAULT}
-    eng = E.Engine(spec["model"], prm, seed=spec["seed"] + rank, stream=stream)
+    first, paths = shard_range(paths, rank)
+    eng = E.Engine(spec["model"], prm, seed=spec["seed"], stream=stream)
     autotune.apply_tuning(eng, knobs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
 
     def one_step():
-        eng.run(paths, dt, n_tr, n_avg)
+        eng.run(paths, dt, n_tr, n_avg, first_path=first)
 
     for _ in range(args.warmup):
         one_step()
@@ -197,7 +231,7 @@ def run_engine(args):
             evs[i][0].record(stream)
             one_step()
             evs[i][1].record(stream)
-            results.append(eng.stats())
+            results.append(combine_sums(eng.stats()["sums"], device="cuda"))
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -212,11 +246,11 @@ def run_engine(args):
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"] + rank,
+        e = E.Engine(spec["model"], E.make_params(**spec["params"]), seed=spec["seed"],
                      stream=stream)
         autotune.apply_tuning(e, knobs)
-        e.run(paths, dt, n_tr, n_avg)
-        e.stats()
+        e.run(paths, dt, n_tr, n_avg, first_path=first)
+        combine_sums(e.stats()["sums"], device="cuda")
         e.close()
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = reduce_max_over_ranks(statistics.median(e2e_times), device="cuda")
@@ -230,12 +264,13 @@ def run_engine(args):
     kernel_s = statistics.mean(times)
     achieved = ALG_SLOTS_PER_PATH_STEP * units / kernel_s / 1e12
     traffic = _profile_traffic(args.workload)
-    st = results[-1]
+    st = ensemble_stats(results[-1], n_avg)        # all ranks' paths: one ensemble
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (Philox seed %d + rank; no dataset in the method)" % spec["seed"],
+        "data": "synthetic (Philox seed %d; rank r runs paths [r 2^20, (r + 1) 2^20) of one "
+                "ensemble; no dataset in the method)" % spec["seed"],
         "config": {"workload": args.workload, "paths_per_gpu": paths,
                    "steps_per_path": steps_per_path, "dt": dt, "n_transient": n_tr,
                    "n_avg": n_avg, "model": "inertial washboard",
@@ -265,8 +300,8 @@ def run_engine(args):
         "gpu_launches": args.steps * (1 + (-(-steps_per_path // knobs["steps_per_launch"])
                                            if knobs["steps_per_launch"] else 1)),
         "clocks": clocks,
-        "result": {"mean_v": st["mean_v"], "stderr_v": st["stderr_v"], "tmean_v": st["tmean_v"],
-                   "tvar_v": st["tvar_v"]},
+        "result": {"ensemble_paths": st["n"], "mean_v": st["mean_v"], "stderr_v": st["stderr_v"],
+                   "tmean_v": st["tmean_v"], "tvar_v": st["tvar_v"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds)

@@ -139,6 +139,18 @@ int sde_run(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_transient, uint6
 int sde_run_paths(sde_ctx* ctx, uint64_t paths, double dt, uint64_t n_transient,
                   uint64_t n_avg, const sde_path_out* out);
 
+/* As sde_run_paths (out may be NULL) for the realisations first_path ..
+ * first_path + paths - 1 of the same ensemble: path i draws its random numbers
+ * with counter path index first_path + i, so disjoint ranges run on several
+ * GPUs (or one after another) give exactly the per-path results of one run
+ * over their union, and the sum of their five FP64 sums (sde_stats_t.sums) is
+ * that run's sums up to the order of FP64 addition.  Eq. 31's ensemble
+ * average needs nothing else to be shared between ranges.  Per-path outputs
+ * are indexed from 0 within the range.  EINVAL if first_path + paths (rounded
+ * up to 32) exceeds 2^32. */
+int sde_run_range(sde_ctx* ctx, uint64_t first_path, uint64_t paths, double dt,
+                  uint64_t n_transient, uint64_t n_avg, const sde_path_out* out);
+
 /* Wait for the last run on the context's stream and return its statistics
  * (host struct `out`).  ESTATE if no run was enqueued. */
 int sde_stats(sde_ctx* ctx, sde_stats_t* out);

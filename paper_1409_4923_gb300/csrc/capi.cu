@@ -445,16 +445,19 @@ int sde_occupancy(sde_ctx* c, int block_threads, int* blocks_per_sm, int* sm_cou
     return SDE_OK;
 }
 
-static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg,
-                    const sde_path_out* out)
+static int run_impl(sde_ctx* c, uint64_t first_path, uint64_t paths, double dt, uint64_t n_tr,
+                    uint64_t n_avg, const sde_path_out* out)
 {
     if (!c) return SDE_EINVAL;
     int rc = validate_run(c, paths, dt, n_tr, n_avg);
     if (rc) return rc;
+    if (first_path > 0xFFFFFFFFull || first_path + ((paths + 31ull) & ~31ull) > 0x100000000ull)
+        return fail(c, SDE_EINVAL, "first_path + paths must stay within the 32-bit path counter");
     const uint64_t items = (paths + 31ull) / 32ull;
     PointConsts P;
     rc = make_point(c, c->model, c->p, dt, paths, n_tr, n_avg, P);
     if (rc) return rc;
+    P.path0 = (uint32_t)first_path;
     const Layout L = layout(1, items, 0);
     if ((rc = ensure_ws(c, L.total))) return rc;
     if ((rc = ensure_host(c, 64))) return rc;
@@ -512,13 +515,19 @@ static int run_impl(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64
 
 int sde_run(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg)
 {
-    return run_impl(c, paths, dt, n_tr, n_avg, nullptr);
+    return run_impl(c, 0, paths, dt, n_tr, n_avg, nullptr);
 }
 
 int sde_run_paths(sde_ctx* c, uint64_t paths, double dt, uint64_t n_tr, uint64_t n_avg,
                   const sde_path_out* out)
 {
-    return run_impl(c, paths, dt, n_tr, n_avg, out);
+    return run_impl(c, 0, paths, dt, n_tr, n_avg, out);
+}
+
+int sde_run_range(sde_ctx* c, uint64_t first_path, uint64_t paths, double dt, uint64_t n_tr,
+                  uint64_t n_avg, const sde_path_out* out)
+{
+    return run_impl(c, first_path, paths, dt, n_tr, n_avg, out);
 }
 
 int sde_stats(sde_ctx* c, sde_stats_t* out)

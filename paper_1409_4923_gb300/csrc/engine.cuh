@@ -54,6 +54,7 @@ struct PointConsts {
     uint32_t c1_init, c1_gauss, c1_pois, c1_dich;   // (tag << 30) | point
     // run
     uint32_t n_tr, n_avg, n_paths;
+    uint32_t path0;     // random-counter index of the run's first path (path ranges)
     double inv_window;  // 1 / (n_avg dt)
     double period;      // spatial period L in x units
     double coord_to_x;  // x = coordinate * coord_to_x (1 / 2 pi for washboards)

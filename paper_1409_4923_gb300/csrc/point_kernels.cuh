@@ -23,24 +23,27 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, t0, (uint32_t)PPT);
         if (item == 0xffffffffu) break;
+        // local: the path's index within the run (outputs); path0 + local:
+        // its index in the random counter
         if (PPT == 1) {
-            const uint32_t path = item * 32u + lane;
-            const bool valid = path < P.n_paths;
+            const uint32_t local = item * 32u + lane;
+            const bool valid = local < P.n_paths;
             PathResult R;
-            simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, path, lane, R);
-            if (valid) store_path(po, path, R);
+            simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, P.path0 + local, lane, R);
+            if (valid) store_path(po, local, R);
             store_partial(partials, item, lane, valid, R);
         } else {
             uint32_t path[PPT];
 #pragma unroll
-            for (int p = 0; p < PPT; ++p) path[p] = (item + (uint32_t)p) * 32u + lane;
+            for (int p = 0; p < PPT; ++p) path[p] = P.path0 + (item + (uint32_t)p) * 32u + lane;
             PathResult R[PPT];
             simulate_paths<MODEL, POIS, DICH, GAUSS, PPT>(P, K, path, lane, R, win);
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
                 if (item + (uint32_t)p >= K.n_items) break;      // past the last item: no output
-                const bool valid = path[p] < P.n_paths;
-                if (valid) store_path(po, path[p], R[p]);
+                const uint32_t local = (item + (uint32_t)p) * 32u + lane;
+                const bool valid = local < P.n_paths;
+                if (valid) store_path(po, local, R[p]);
                 store_partial(partials, item + (uint32_t)p, lane, valid, R[p]);
             }
         }

@@ -23,17 +23,18 @@ __global__ void __launch_bounds__(128) segment_kernel(const __grid_constant__ Po
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, 0ull);
         if (item == 0xffffffffu) break;
-        const uint32_t path = item * 32u + lane;
+        const uint32_t local = item * 32u + lane;       // state plane and output index
+        const uint32_t path = P.path0 + local;           // random-counter index
         PathState S;
         if (na == 0u) init_path<MODEL, POIS, DICH>(S, P, K, path);
-        else load_state(S, M, path);
+        else load_state(S, M, local);
         advance_path<MODEL, POIS, DICH, GAUSS>(S, P, K, path, lane, na, nb);
-        store_state(S, M, path);
+        store_state(S, M, local);
         if (last) {
-            const bool valid = path < P.n_paths;
+            const bool valid = local < P.n_paths;
             PathResult R;
             finish_path<MODEL, POIS, DICH>(S, P, R);
-            if (valid) store_path(po, path, R);
+            if (valid) store_path(po, local, R);
             store_partial(partials, item, lane, valid, R);
         }
     }

@@ -83,6 +83,8 @@ def lib():
                                    ctypes.c_uint64]),
         "sde_run_paths": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.POINTER(PathOut)]),
+        "sde_run_range": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(PathOut)]),
         "sde_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
         "sde_scan": (ctypes.c_int, [_P, ctypes.POINTER(ScanPoint), ctypes.c_uint32,
                                     ctypes.POINTER(Stats), ctypes.c_double]),
@@ -209,9 +211,15 @@ class Engine:
             setattr(po, name, t.data_ptr())
         return po
 
-    def run(self, paths, dt, n_transient, n_avg, path_out=None):
+    def run(self, paths, dt, n_transient, n_avg, path_out=None, first_path=0):
         """Enqueue a run; path_out: dict of torch CUDA tensors (X_f f64, v_f f32, vbar f64,
-        jP u32/i32, jD u32/i32), each of length `paths`."""
+        jP u32/i32, jD u32/i32), each of length `paths`.  first_path > 0 runs the
+        realisations first_path .. first_path + paths - 1 (sde_run_range)."""
+        if first_path:
+            po = None if path_out is None else ctypes.byref(self._path_out(path_out, paths))
+            _check(self._ctx, lib().sde_run_range(self._ctx, int(first_path), int(paths), float(dt),
+                                                  int(n_transient), int(n_avg), po))
+            return
         if path_out is None:
             _check(self._ctx, lib().sde_run(self._ctx, int(paths), float(dt), int(n_transient),
                                             int(n_avg)))
