@@ -194,3 +194,157 @@ def test_gradients_match_oracle(S):
     for name in ("b2", "W3"):
         ok = 0.05 * np.abs(G0[name]) > K_SIGMA * sigma[name]
         assert ok.mean() > 0.5, (name, ok.mean())
+
+
+
+def test_adam_first_step(S):
+    """t = 1: every live parameter moves by -lr sign(g) where the oracle's
+    gradient is clearly non-zero (Adam's closed-form first step)."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 5)
+    rng = np.random.default_rng(6)
+    M, lr = 512, 1e-3
+    x = _raw_inputs(rng, M)
+    t = np.stack([rng.normal(0.1, 0.2, M), rng.normal(-3.0, 1.5, M)], axis=1)
+    try:
+        net.train_step(torch.from_numpy(x.astype(np.float32)).cuda(),
+                       torch.from_numpy(t.astype(np.float32)).cuda(), lr)
+        q = net.get_params().astype(np.float64)
+    finally:
+        net.close()
+    pb = bf16_round(p)
+    xp = omlp.input_map(x.astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    _, g0 = omlp.loss_and_grad(pb, xp, (t.astype(np.float32) - osh) / osc)
+    big = np.abs(g0) > 1e-3 * np.abs(g0).max()
+    step = q - p.astype(np.float32).astype(np.float64)
+    agree = np.abs(step[big] + lr * np.sign(g0[big])) <= 1e-6
+    assert agree.mean() > 0.97, agree.mean()
+    assert np.all(step[~big & (g0 == 0)] == 0)
+
+
+def test_training_fits_a_smooth_function(S):
+    rng = np.random.default_rng(7)
+    N = 1 << 14
+    x = _raw_inputs(rng, N)
+    u = (x - x.min(0)) / (x.max(0) - x.min(0))
+    t = np.stack([np.sin(3 * u[:, 3]) * np.cos(2 * u[:, 1]) + 0.5 * u[:, 0] * u[:, 6],
+                  np.log10(x[:, 4]) + u[:, 2] ** 2], axis=1)
+    net = S.Surrogate(8)
+    try:
+        lo = np.array([0.5, 2.0, 3.0, -0.3, -4.0, 0.1, 0.01])
+        hi = np.array([1.5, 6.0, 7.0, 0.3, -1.0, 5.0, 0.5])
+        net.set_maps((lo + hi) / 2, 2.0 / (hi - lo), 1 << 4, t.mean(0), t.std(0))
+        X = torch.from_numpy(x.astype(np.float32)).cuda()
+        T = torch.from_numpy(t.astype(np.float32)).cuda()
+        hist = net.fit(X, T, steps=1500, batch=1024, lr=2e-3)
+        y = net.forward(X).cpu().numpy()
+    finally:
+        net.close()
+    assert hist[-50:].mean() < 0.05 * hist[:50].mean()
+    rmse = np.sqrt(np.mean((y - t) ** 2, axis=0)) / t.std(0)
+    assert np.all(rmse < 0.15), rmse
+
+
+def _cosine_lr(lr, lr_final, k, steps):
+    return lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+
+
+def test_fit_full_batch_matches_train_steps(S):
+    """sde_mlp_fit with one minibatch per epoch (batch = N) against as many
+    sde_mlp_train_step calls on the rows in their natural order, with the host's
+    cosine learning rates.  The epoch's shuffled order must be a permutation of
+    the rows (the loss before the first update is the full-data loss; a
+    duplicated or missing row would move it by about 1/N), and the graph-replayed
+    schedule and Adam corrections those of the host loop.  Only the summation
+    order of the gradients' row reductions differs."""
+    rng = np.random.default_rng(21)
+    N, steps, lr, lr_final = 200, 6, 2e-3, 2e-4
+    x = torch.from_numpy(_raw_inputs(rng, N).astype(np.float32)).cuda()
+    t = torch.from_numpy(np.stack([rng.normal(0.1, 0.2, N), rng.normal(-3.0, 1.5, N)],
+                                  axis=1).astype(np.float32)).cuda()
+    nets = [_random_net(S, 22)[0] for _ in range(2)]
+    try:
+        hist = nets[0].fit(x, t, steps=steps, batch=N, lr=lr, lr_final=lr_final, seed=5)
+        ref = torch.zeros(steps, dtype=torch.float32, device="cuda")
+        for k in range(steps):
+            nets[1].train_step(x, t, _cosine_lr(lr, lr_final, k, steps), loss_out=ref[k:k + 1])
+        ref = ref.cpu().numpy()
+        pa = nets[0].get_params().astype(np.float64)
+        pb = nets[1].get_params().astype(np.float64)
+    finally:
+        for n in nets:
+            n.close()
+    np.testing.assert_allclose(hist[0], ref[0], rtol=1e-6)
+    np.testing.assert_allclose(hist, ref, rtol=1e-5)
+    assert hist[-1] < hist[0]
+    # parameters: equal up to the reduction order (a weight whose gradient is
+    # at rounding level may take Adam's sign step the other way)
+    assert np.mean(np.abs(pa - pb) > 1e-5) < 0.01
+
+
+def test_fit_rejects_bad_arguments(S):
+    net = S.Surrogate(3)
+    try:
+        x = torch.zeros((16, 7), dtype=torch.float32, device="cuda")
+        t = torch.zeros((16, 2), dtype=torch.float32, device="cuda")
+        for kw in (dict(steps=0), dict(lr=0.0), dict(lr_final=-1.0)):
+            with pytest.raises(Exception):
+                net.fit(x, t, **dict(dict(steps=2, batch=8), **kw))
+        rc = net._L.sde_mlp_fit(net._net, S._ptr(x), S._ptr(t), 16, 2, 17, 1e-3, 1e-4, 0.9, 0.999, 1e-8, 0, None)
+        assert rc != 0                                           # batch > N
+    finally:
+        net.close()
+
+
+def test_tcgen05_forward_matches_mma_path_and_oracle(S):
+    """The fused tcgen05 forward (maps and layers 1-2; layers 3-4 and the
+    output map; FP32 accumulators in tensor memory, two per CTA) against the
+    layer-by-layer mma.sync kernels and the FP64 oracle, over a row count of
+    521 tiles (several per CTA) ending in a ragged 128-row tile."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 9)
+    rng = np.random.default_rng(10)
+    M = 65536 + 1000 + 37
+    x = _raw_inputs(rng, M)
+    X = torch.from_numpy(x.astype(np.float32)).cuda()
+    try:
+        net.set_tensor_path(1)
+        y_tc = net.forward(X)
+        net.sync()
+        net.set_tensor_path(0)
+        y_mma = net.forward(X)
+        net.sync()
+        y_tc, y_mma = y_tc.cpu().numpy(), y_mma.cpu().numpy()
+    finally:
+        net.close()
+    rms = np.sqrt(np.mean(((y_mma - osh) / osc) ** 2, axis=0))
+    d = np.abs(y_tc - y_mma) / osc / rms
+    assert np.isfinite(y_tc).all() and d.max() < 0.01, d.max()
+    sel = np.concatenate([np.arange(300), np.arange(M - 300, M)])
+    xp = omlp.input_map(x[sel].astype(np.float32).astype(np.float64), shift.astype(np.float32),
+                        scale.astype(np.float32), mask)
+    yp, _ = omlp.forward(bf16_round(p), xp)
+    err = np.abs(y_tc[sel] - (yp * osc + osh)) / osc / np.sqrt(np.mean(yp ** 2, axis=0))
+    assert err.max() < 0.03, err.max()
+
+
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 152 * 128 + 5])
+def test_tcgen05_forward_edge_sizes(S, M):
+    """One row, a tile short of full, exactly one tile, one row past it, and
+    one more tile than SMs: the fused path agrees with the mma.sync path."""
+    net, p, (shift, scale, mask, osh, osc) = _random_net(S, 12)
+    x = _raw_inputs(np.random.default_rng(M), M)
+    X = torch.from_numpy(x.astype(np.float32)).cuda()
+    try:
+        net.set_tensor_path(1)
+        y_tc = net.forward(X)
+        net.sync()
+        net.set_tensor_path(0)
+        y_mma = net.forward(X)
+        net.sync()
+        y_tc, y_mma = y_tc.cpu().numpy(), y_mma.cpu().numpy()
+    finally:
+        net.close()
+    assert y_tc.shape == (M, 2) and np.isfinite(y_tc).all()
+    d = np.abs(y_tc - y_mma) / osc
+    assert d.max() < 0.02, d.max()
+
