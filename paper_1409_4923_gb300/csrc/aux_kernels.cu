@@ -93,6 +93,12 @@ __global__ void __launch_bounds__(128, 6) scan_kernel(const PointConsts* __restr
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t t0 = K.budget_ns ? globaltimer_ns() : 0ull;
+    constexpr bool kKickWin = WindowedKicks<POIS, GAUSS>::value;
+    uint32_t* win = nullptr;
+    if constexpr (kKickWin) {
+        extern __shared__ uint32_t sde_scan1_smem[];
+        win = sde_scan1_smem + (threadIdx.x >> 5) * kKickWordsPerWarp + lane;
+    }
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, t0);
         if (item == 0xffffffffu) break;
@@ -101,7 +107,7 @@ __global__ void __launch_bounds__(128, 6) scan_kernel(const PointConsts* __restr
         const uint32_t path = it.y + lane;
         const bool valid = path < P.n_paths;
         PathResult R;
-        simulate_path<kModelInertial, POIS, DICH, GAUSS>(P, K, path, lane, R);
+        simulate_path<kModelInertial, POIS, DICH, GAUSS, kKickWin>(P, K, path, lane, R, win);
         store_partial(partials, item, lane, valid, R);
     }
 }
@@ -111,9 +117,11 @@ static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, con
                                  const Workspace& ws, int bt, int gb, int sm, cudaStream_t st)
 {
     auto kern = scan_kernel<POIS, DICH, GAUSS>;
+    const size_t smem = WindowedKicks<POIS, GAUSS>::value
+                            ? (size_t)(bt / 32) * kKickWordsPerWarp * sizeof(uint32_t) : 0u;
     if (gb <= 0) {
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bt, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bt, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
         const uint64_t need = ((uint64_t)K.n_items * 32ull + bt - 1) / bt;
@@ -121,7 +129,7 @@ static cudaError_t launch_scan_t(const PointConsts* pts, const uint2* items, con
         gb = (int)(need < cap ? need : cap);
         if (gb < 1) gb = 1;
     }
-    kern<<<gb, bt, 0, st>>>(pts, items, K, ws.counter, ws.status, ws.partials);
+    kern<<<gb, bt, smem, st>>>(pts, items, K, ws.counter, ws.status, ws.partials);
     return cudaGetLastError();
 }
 

@@ -413,6 +413,51 @@ __device__ __forceinline__ float gauss_at(const PointConsts& P, const LaunchCons
     return dxi;
 }
 
+// Poissonian kicks drawn a window of chunks ahead, the counterpart of the
+// dichotomous flip window below: per 32-step chunk a path has 0.41 kicks at
+// lambda dt = 0.0128, but the warp's per-chunk event loop runs as often as its
+// busiest lane needs.  Per window of kKickWinChunks chunks (512 steps) each
+// lane draws its kicks once: bit i of mask word c marks a kick at step
+// n0 + 32 c + i, and the kicks' increments (Algorithm 3: z - a dt) follow in
+// kick order.  The queue holds kKickQueue increments; a lane whose queue fills
+// up before the window's end shortens the window of the whole warp, which
+// then draws its kicks again from the saved event state (the draws are a
+// function of the event index, so the second pass gives the same kicks).  A
+// chunk holds at most 32 kicks, so a window always keeps at least one chunk.
+// The steps then pop the increments in order, with no per-chunk limit.
+constexpr uint32_t kKickWinChunks = 16;
+constexpr uint32_t kKickQueue = 32;
+// Per lane: kKickWinChunks mask words, then kKickQueue + 1 increments (the
+// last is read ahead after the final kick and never used), word-major with a
+// stride of 32 so that each access is one word per lane.
+constexpr uint32_t kKickWordsPerLane = kKickWinChunks + kKickQueue + 1u;
+constexpr uint32_t kKickWordsPerWarp = kKickWordsPerLane * 32u;
+
+// Kick windows run in the one-path-per-lane chunk loop of the point and scan
+// kernels (not in segmented runs, whose saved state is the next event).
+template <bool POIS, int GAUSS>
+struct WindowedKicks { static constexpr bool value = POIS && GAUSS != kGaussNormal; };
+
+// Kicks of one path in the steps [n0, wend) into the lane's words tw (stride
+// 32): masks in words 0 .. kKickWinChunks - 1, increments from word
+// kKickWinChunks.  Returns wend, or the step of the first kick not drawn when
+// the queue filled up first; S then holds that kick as its next event.
+__device__ __forceinline__ uint32_t window_kicks(PathState& S, const PointConsts& P, const LaunchConsts& K,
+                                                 uint32_t path, uint32_t n0, uint32_t wend, uint32_t* tw)
+{
+#pragma unroll
+    for (uint32_t c = 0; c < kKickWinChunks; ++c) tw[c * 32u] = 0u;
+    float* tq = (float*)(tw + kKickWinChunks * 32u);
+    uint32_t cnt = 0u;
+    while (S.eP < wend && cnt < kKickQueue) {
+        const uint32_t off = S.eP - n0;
+        tw[(off >> 5) * 32u] |= 1u << (off & 31u);
+        tq[cnt * 32u] = pois_event(S, P, K, path);
+        ++cnt;
+    }
+    return S.eP < wend ? S.eP : wend;
+}
+
 // Steps n in [n, n_end) one at a time (phase edges that are not whole
 // 32-step chunks).
 template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC>
@@ -435,18 +480,21 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 // first block (group); each block (group) draws the next one's words while it
 // integrates, so the Philox multiplies interleave with the step arithmetic,
 // and w returns holding those that follow the chunk.
-template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST>
+// With QUEUE the kick increments come from the lane's window queue tq
+// (stride 32) from index qi on, z0 holding the next one; qi advances.
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST, bool QUEUE = false>
 __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                             uint32_t path, uint32_t n0, float dch, float& dcur,
                                             uint4& w, uint32_t pm, float z0, float z1, float z2,
-                                            uint32_t dm)
+                                            uint32_t dm, const float* tq = nullptr,
+                                            uint32_t* qi = nullptr, float* zq = nullptr)
 {
     // Without Box-Muller words the chunk is two 16-step blocks of one Philox
     // call each: the block's four groups are unrolled, so each group's word
     // and each step's event bit are compile-time selections.  The rare chunks
     // whose Poisson events take the inline path keep the compact loop of one
     // group per iteration below.
-    constexpr bool kBlockLoop = GAUSS != kGaussNormal && (!POIS || FAST);
+    constexpr bool kBlockLoop = GAUSS != kGaussNormal && (!POIS || FAST || QUEUE);
     if (kBlockLoop) {
 #pragma unroll 1
         for (uint32_t b = 0; b < 2u; ++b) {
@@ -460,7 +508,14 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
                     const float dnext = __shfl_sync(0xffffffffu, dch, (int)(q * 4u + k));
                     const float dxi = GAUSS == kGauss3Point ? three_point(r, P) : 0.0f;
                     float pj = 0.0f, dg = 0.0f;
-                    if (POIS) {
+                    if (POIS && QUEUE) {
+                        const bool kick = (pm & (1u << (q * 4u + k))) != 0u;
+                        pj = kick ? *zq : -P.aP_dt;
+                        if (kick) {
+                            ++*qi;
+                            *zq = tq[*qi * 32u];
+                        }
+                    } else if (POIS) {
                         const bool kick = (pm & (1u << (q * 4u + k))) != 0u;
                         pj = kick ? z0 : -P.aP_dt;
                         z0 = kick ? z1 : z0;
@@ -527,9 +582,12 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
 // Chunks and flushes sit at absolute step positions, so a run cut into
 // segments at multiples of 32 steps takes the same arithmetic as one launch.
 // All 32 lanes of the warp must call this together.
-template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC>
+// WIN: the Poissonian kicks are drawn in windows (WindowedKicks), in the
+// lane's kKickWordsPerLane words of shared memory at win (stride 32).
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool WIN = false>
 __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
-                                          uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end)
+                                          uint32_t path, uint32_t lane, uint32_t n, uint32_t n_end,
+                                          uint32_t* win = nullptr)
 {
     uint32_t head = n;                                   // first chunk boundary
     if ((n & 31u) != 0u) head = min(n_end, (n + 31u) & ~31u);
@@ -542,6 +600,40 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (GAUSS == kGauss3Point) w = stream(K, P.c1_gauss, path, n >> 4);
         else if (GAUSS == kGaussNormal) w = stream(K, P.c1_gauss, path, n >> 2);
+        if constexpr (WIN && WindowedKicks<POIS, GAUSS>::value) {
+            uint32_t* tw = win;
+            const float* tq = (const float*)(win + kKickWinChunks * 32u);
+            while (n + 32u <= n_end) {
+                uint32_t wend = n + 32u * min(kKickWinChunks, (n_end - n) >> 5);
+                const uint32_t e_s = S.eP, j_s = S.JP, w2_s = S.pw2, w3_s = S.pw3;
+                const uint32_t cover = __reduce_min_sync(0xffffffffu, window_kicks(S, P, K, path, n, wend, tw));
+                if (cover < wend) {
+                    // a lane's queue filled up: the warp's window ends at the last
+                    // whole chunk that every lane covers (at least one), drawn again
+                    wend = n + ((cover - n) & ~31u);
+                    S.eP = e_s; S.JP = j_s; S.pw2 = w2_s; S.pw3 = w3_s;
+                    window_kicks(S, P, K, path, n, wend, tw);
+                }
+                uint32_t qi = 0u;
+                float zq = tq[0];
+#pragma unroll 1
+                for (const uint32_t* pmw = tw; n < wend; n += 32u, pmw += 32) {
+                    const float dch = drive_at(n + 1u + lane, P);
+                    uint32_t pm_unused, dm;
+                    float z0, z1, z2;
+                    chunk_events<false, DICH>(S, P, K, path, n, pm_unused, z0, z1, z2, dm);
+                    chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, true, true>(S, P, K, path, n, dch, dcur, w,
+                                                                           *pmw, z0, z1, z2, dm, tq, &qi,
+                                                                           &zq);
+                    if (ACC && ((n + 32u) & 255u) == 0u) {
+                        S.svd += (double)S.sv;
+                        S.sv2d += (double)S.sv2;
+                        S.sv = 0.0f;
+                        S.sv2 = 0.0f;
+                    }
+                }
+            }
+        } else
         for (; n + 32u <= n_end; n += 32u) {
             const float dch = drive_at(n + 1u + lane, P);
             uint32_t pm, dm;
@@ -614,18 +706,21 @@ __device__ __forceinline__ void finish_path(const PathState& S, const PointConst
     R.jD = DICH ? S.JD - 1u : 0u;
 }
 
-template <int MODEL, bool POIS, int DICH, int GAUSS>
+// WIN: draw the Poissonian kicks in windows, in the lane's shared-memory
+// words at win (see WindowedKicks).
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool WIN = false>
 __device__ __forceinline__ void simulate_path(const PointConsts& P, const LaunchConsts& K,
-                                              uint32_t path, uint32_t lane, PathResult& R)
+                                              uint32_t path, uint32_t lane, PathResult& R,
+                                              uint32_t* win = nullptr)
 {
     PathState S;
     init_path<MODEL, POIS, DICH>(S, P, K, path);
-    run_steps<MODEL, POIS, DICH, GAUSS, false>(S, P, K, path, lane, 0u, P.n_tr);
+    run_steps<MODEL, POIS, DICH, GAUSS, false, WIN>(S, P, K, path, lane, 0u, P.n_tr, win);
     if (!FoldPerStep<MODEL>::value) fold<MODEL>(S);
     S.c_i = S.c;
     S.kf_i = S.kf;
-    run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial>(S, P, K, path, lane, P.n_tr,
-                                                                 P.n_tr + P.n_avg);
+    run_steps<MODEL, POIS, DICH, GAUSS, MODEL == kModelInertial, WIN>(S, P, K, path, lane, P.n_tr,
+                                                                      P.n_tr + P.n_avg, win);
     finish_path<MODEL, POIS, DICH>(S, P, R);
 }
 

@@ -20,6 +20,11 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
         extern __shared__ uint32_t sde_point_smem[];
         win = sde_point_smem + (threadIdx.x >> 5) * kWinWordsPerWarp;
     }
+    constexpr bool kKickWin = PPT == 1 && WindowedKicks<POIS, GAUSS>::value;
+    if constexpr (kKickWin) {
+        extern __shared__ uint32_t sde_point_smem[];
+        win = sde_point_smem + (threadIdx.x >> 5) * kKickWordsPerWarp + lane;
+    }
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, t0, (uint32_t)PPT);
         if (item == 0xffffffffu) break;
@@ -29,7 +34,7 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
             const uint32_t local = item * 32u + lane;
             const bool valid = local < P.n_paths;
             PathResult R;
-            simulate_path<MODEL, POIS, DICH, GAUSS>(P, K, P.path0 + local, lane, R);
+            simulate_path<MODEL, POIS, DICH, GAUSS, kKickWin>(P, K, P.path0 + local, lane, R, win);
             if (valid) store_path(po, local, R);
             store_partial(partials, item, lane, valid, R);
         } else {
@@ -84,12 +89,15 @@ constexpr auto point_kernel_for()
     else return point_kernel<MODEL, POIS, DICH, GAUSS, PPT>;
 }
 
-// Dynamic shared memory of a launch: the flip windows of its warps.
+// Dynamic shared memory of a launch: the flip or kick windows of its warps.
 template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 constexpr size_t point_smem_bytes(int block_threads)
 {
-    return WindowedFlips<MODEL, POIS, DICH, GAUSS, PPT>::value
-               ? (size_t)(block_threads / 32) * kWinWordsPerWarp * sizeof(uint32_t) : 0u;
+    if (WindowedFlips<MODEL, POIS, DICH, GAUSS, PPT>::value)
+        return (size_t)(block_threads / 32) * kWinWordsPerWarp * sizeof(uint32_t);
+    if (PPT == 1 && WindowedKicks<POIS, GAUSS>::value)
+        return (size_t)(block_threads / 32) * kKickWordsPerWarp * sizeof(uint32_t);
+    return 0u;
 }
 
 template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
