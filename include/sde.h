@@ -180,6 +180,17 @@ typedef struct {
 int sde_scan(sde_ctx* ctx, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out,
              double deadline_ms);
 
+/* The batched scan of sde_scan with its results left on the device, for
+ * screens that chain on the GPU without a host round trip (Sec. 5: many
+ * parameter values per kernel call).  Enqueues the scan on the context's
+ * stream and returns without synchronising: the host array pts is copied at
+ * the call.  out5 is a caller-owned DEVICE array of 5 * npts doubles that
+ * receives, per point in the order of pts, the FP64 sums of sde_stats_t.sums
+ * (paths, sum of Eq. 31's quotient, its sum of squares, sum v, sum v^2 over
+ * the averaging window); they equal sde_scan's bit for bit.  No deadline.
+ * EINVAL on bad arguments (as sde_scan), ENOMEM / ECUDA on device failure. */
+int sde_scan_device(sde_ctx* ctx, const sde_scan_point* pts, uint32_t npts, double* out5);
+
 /* Continue the last sde_scan of this context after it returned
  * SDE_ETIMEDOUT: the work items that it did not start run now, under a fresh
  * deadline_ms (0 = none); the items it finished are kept.  Each item's result

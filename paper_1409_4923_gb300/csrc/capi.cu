@@ -114,7 +114,8 @@ struct sde_ctx {
     void* run_state = nullptr;    // saved states of runs cut into launches
     size_t run_state_bytes = 0;
     // scan graphs keyed by (npts, n_items, flags, budget)
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, ScanGraph> graphs;
+    // (and the caller's device output array of sde_scan_device, 0 for sde_scan)
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t, uint64_t>, ScanGraph> graphs;
     // bumped by every call that writes the workspace; a timed-out scan can be
     // resumed only while its workspace is untouched
     uint64_t ws_gen = 0;
@@ -541,9 +542,13 @@ int sde_stats(sde_ctx* c, sde_stats_t* out)
     return status == kStatusOk ? SDE_OK : fail(c, SDE_ETIMEDOUT, "device deadline expired");
 }
 
-int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out, double deadline_ms)
+// The batched scan.  Host mode (dev_out5 == NULL): statistics to the host
+// array `out`, synchronising.  Device mode: each point's five FP64 sums to
+// the caller's device array dev_out5, enqueued only (no deadline).
+static int scan_impl(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out,
+                     double deadline_ms, double* dev_out5)
 {
-    if (!c || (!pts && npts) || (!out && npts)) return SDE_EINVAL;
+    if (!c || (!pts && npts) || (!out && !dev_out5 && npts)) return SDE_EINVAL;
     if (npts == 0) return SDE_OK;
     if (!(deadline_ms >= 0.0) || !std::isfinite(deadline_ms)) return fail(c, SDE_EINVAL, "deadline_ms must be >= 0");
     const uint32_t flags = pts[0].p.noise_flags;
@@ -608,7 +613,7 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
     int32_t* h_status = (int32_t*)(c->host + 5 * npts);
     if (use_scan_kernel) {
         const LaunchConsts K = make_launch(c->seed, (uint32_t)total_items, budget);
-        auto key = std::make_tuple(npts, (uint32_t)total_items, flags, budget);
+        auto key = std::make_tuple(npts, (uint32_t)total_items, flags, budget, (uint64_t)(uintptr_t)dev_out5);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end() || c->stream == nullptr) {
             ScanGraph g;
@@ -623,10 +628,10 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
                 e = launch_scan((flags & SDE_NOISE_POISSON) != 0, dich_kind(flags),
                                 (flags & SDE_NOISE_GAUSS) ? kGauss3Point : 0, d_pts,
                                 d_items, K, ws, c->block_threads, c->grid_blocks, c->sm_count, c->stream);
-            if (e == cudaSuccess) e = launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) e = launch_fold(ws.partials, d_ranges, npts, dev_out5 ? dev_out5 : d_out5, c->stream);
+            if (e == cudaSuccess && !dev_out5)
                 e = cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * npts, cudaMemcpyDeviceToHost, c->stream);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && !dev_out5)
                 e = cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
             if (capture) {
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &g.graph);
@@ -658,10 +663,13 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
                                      c->paths_per_thread, P[i], K, wsi,
                                      po, c->block_threads, c->grid_blocks, c->sm_count, c->stream));
         }
-        SDE_CUDA(c, launch_fold(ws.partials, d_ranges, npts, d_out5, c->stream));
-        SDE_CUDA(c, cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * npts, cudaMemcpyDeviceToHost, c->stream));
-        SDE_CUDA(c, cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        SDE_CUDA(c, launch_fold(ws.partials, d_ranges, npts, dev_out5 ? dev_out5 : d_out5, c->stream));
+        if (!dev_out5) {
+            SDE_CUDA(c, cudaMemcpyAsync(h_out, d_out5, sizeof(double) * 5 * npts, cudaMemcpyDeviceToHost, c->stream));
+            SDE_CUDA(c, cudaMemcpyAsync(h_status, ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        }
     }
+    if (dev_out5) return SDE_OK;          // device mode: enqueued only
     SDE_CUDA(c, cudaStreamSynchronize(c->stream));
     const int32_t status = *h_status;
     for (uint32_t i = 0; i < npts; ++i) fill_stats(h_out + 5ull * i, status, pts[i].n_avg, &out[i]);
@@ -689,6 +697,17 @@ int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* 
     S.ranges = ranges;
     S.P = P;
     return fail(c, SDE_ETIMEDOUT, "device deadline expired");
+}
+
+int sde_scan(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_stats_t* out, double deadline_ms)
+{
+    return scan_impl(c, pts, npts, out, deadline_ms, nullptr);
+}
+
+int sde_scan_device(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, double* out5)
+{
+    if (c && npts && !out5) return fail(c, SDE_EINVAL, "out5 is NULL");
+    return scan_impl(c, pts, npts, nullptr, 0.0, out5);
 }
 
 int sde_scan_resume(sde_ctx* c, sde_stats_t* out, double deadline_ms)

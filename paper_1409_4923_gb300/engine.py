@@ -89,6 +89,7 @@ def lib():
         "sde_scan": (ctypes.c_int, [_P, ctypes.POINTER(ScanPoint), ctypes.c_uint32,
                                     ctypes.POINTER(Stats), ctypes.c_double]),
         "sde_scan_resume": (ctypes.c_int, [_P, ctypes.POINTER(Stats), ctypes.c_double]),
+        "sde_scan_device": (ctypes.c_int, [_P, ctypes.POINTER(ScanPoint), ctypes.c_uint32, _P]),
         "sde_begin": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64,
                                      ctypes.c_uint64]),
         "sde_advance": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(PathOut),
@@ -279,6 +280,21 @@ class Engine:
         self._scan_n = n
         _check(self._ctx, lib().sde_scan(self._ctx, arr, n, out, float(deadline_ms)))
         return [o.as_dict() for o in out]
+
+    def scan_device(self, points, out5):
+        """sde_scan_device: enqueue the scan; out5 (CUDA float64 tensor of >= 5 * len(points)
+        elements) receives each point's five FP64 sums.  Does not synchronise."""
+        n = len(points)
+        if not out5.is_cuda or out5.dtype.itemsize != 8 or out5.numel() < 5 * n or not out5.is_contiguous():
+            raise ValueError("out5 must be a contiguous CUDA float64 tensor of >= 5 * npts elements")
+        arr = (ScanPoint * n)()
+        for i, pt in enumerate(points):
+            arr[i].p = pt["params"]
+            arr[i].dt = float(pt["dt"])
+            arr[i].paths = int(pt["paths"])
+            arr[i].n_transient = int(pt["n_transient"])
+            arr[i].n_avg = int(pt["n_avg"])
+        _check(self._ctx, lib().sde_scan_device(self._ctx, arr, n, ctypes.c_void_p(out5.data_ptr())))
 
     def scan_resume(self, deadline_ms=0.0):
         """Finish the last scan after it raised SdeTimeout (items already done are kept)."""

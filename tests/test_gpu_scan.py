@@ -103,3 +103,26 @@ def test_deadline_times_out_and_context_survives(E, W):
         assert all(r["status"] == 0 for r in res)
     finally:
         eng.close()
+
+
+@pytest.mark.parametrize("flags", [None, 5])
+def test_scan_device_outputs_equal_host_scan(E, W, flags):
+    """sde_scan_device leaves each point's five sums in a device array (no host
+    round trip): the same values as sde_scan, bit for bit, also when the two
+    calls alternate (each keeps its own captured graph)."""
+    pts = _points(E, W, flags)
+    arg = [dict(p, params=E.make_params(**p["params"])) for p in pts]
+    eng = E.Engine(0, arg[0]["params"], seed=4)
+    try:
+        out5 = torch.full((5 * len(arg),), float("nan"), dtype=torch.float64, device="cuda")
+        eng.scan_device(arg, out5)
+        host = eng.scan(arg)
+        out5b = torch.zeros_like(out5)
+        eng.scan_device(arg, out5b)
+        torch.cuda.synchronize()
+    finally:
+        eng.close()
+    d, db = out5.cpu().numpy().reshape(-1, 5), out5b.cpu().numpy().reshape(-1, 5)
+    for i, h in enumerate(host):
+        assert list(d[i]) == h["sums"]
+        assert list(db[i]) == h["sums"]
