@@ -317,8 +317,9 @@ def run_engine(args):
 def scan_record(n_valid, device_index):
     """The metric's second half, measured after the timed path-steps region:
     points per second at |d<v>| <= 0.01 of the surrogate-guided 1024 x 1024
-    dichotomous scan against plain Monte Carlo on the same grid, and the
-    64 x 64 Poissonian batched scan (one persistent launch).
+    dichotomous scan against plain Monte Carlo on the same grid, the 64 x 64
+    Poissonian batched scan (one persistent launch), and that scan screened by
+    networks of its own 2-D slice, validated on all of its points.
 
     Plain Monte Carlo is measured, not assumed: n_valid random grid points run
     through the same batched scan at the plain map's 8192 paths (their values
@@ -326,10 +327,11 @@ def scan_record(n_valid, device_index):
     plain method's points/s and the guided map's error on those points.  The
     plain map's full cost is extrapolated from that rate:
     t_plain_map = grid points / (n_valid / t_valid)."""
-    from paper_1409_4923_gb300 import guided, timing
+    from paper_1409_4923_gb300 import box_surrogate, guided, timing
     with ClockSampler(device_index) as clk:
         g = guided.guided_dichot_scan(n_valid=n_valid, log=lambda *a: None)
         s64 = timing.time_scan("scan_64x64", reps=2)
+        gp = box_surrogate.slice_screen_64x64()
     npts = g["grid"][0] * g["grid"][1]
     t = g["seconds"]
     plain_pps = g["points_per_s_plain"]
@@ -367,6 +369,18 @@ def scan_record(n_valid, device_index):
                        "seconds": s64["seconds"], "points_per_s": s64["points_per_s"],
                        "path_steps_per_s": s64["path_steps_per_s"],
                        "launch_shape": s64["launch_shape"]},
+        "guided_64x64_poisson": {
+            "workload": "the same 4096 points screened by networks of the (F, log Q) slice; every "
+                        "point validated against the plain map",
+            "labels": gp["labels"], "flagged_fraction": gp["flagged_fraction"],
+            "max_abs_err": gp["max_abs_err"], "frac_within_0.01": gp["frac_within_0.01"],
+            "path_steps_guided_total": gp["path_steps_guided_total"],
+            "path_steps_plain_map": gp["path_steps_plain_map"],
+            "ratio_path_steps_plain_over_guided": gp["ratio_plain_over_guided_total"],
+            "seconds_guided_total": gp["seconds_guided_total"],
+            "points_per_s_guided": 4096.0 / gp["seconds_guided_total"],
+            "seconds_plain_map": gp["seconds_plain_map"],
+            "points_per_s_plain": 4096.0 / gp["seconds_plain_map"]},
         "clocks": clk.summary(),
     }
 

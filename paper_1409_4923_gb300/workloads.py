@@ -90,10 +90,19 @@ SURROGATE_KEYS = ("gamma", "a", "omega", "F", "log10Q", "lambda", "zeta")
 
 
 def surrogate_box_points(n=1 << 17, spp=100, transient_periods=100, avg_periods=400, paths=4096,
-                         stream=2):
-    """Uniform draws in the 7-D box; returns (X[n,7] raw inputs, list of scan points)."""
+                         stream=2, edge_fraction=0.0):
+    """Draws in the 7-D box; returns (X[n,7] box coordinates with log10 Q, list of
+    scan points).  A fraction edge_fraction of the points has each coordinate
+    drawn from the arcsine law (density 1 / (pi sqrt(u (1 - u))) on the unit
+    interval), which samples the box's faces more densely; the rest is uniform."""
     rng = _rng(stream)
-    X = np.stack([rng.uniform(*SURROGATE_BOX[k], n) for k in SURROGATE_KEYS], axis=1)
+    U = rng.uniform(0.0, 1.0, (n, len(SURROGATE_KEYS)))
+    if edge_fraction > 0.0:
+        edge = rng.uniform(0.0, 1.0, n) < edge_fraction
+        U[edge] = 0.5 - 0.5 * np.cos(np.pi * U[edge])
+    lo = np.array([SURROGATE_BOX[k][0] for k in SURROGATE_KEYS])
+    hi = np.array([SURROGATE_BOX[k][1] for k in SURROGATE_KEYS])
+    X = lo + (hi - lo) * U
     pts = []
     for i in range(n):
         g, a, w, F, lq, lam, zeta = X[i]

@@ -37,4 +37,24 @@ def test_box_surrogate_pipeline_small():
     assert r["labels"] == 2048 + 256 and r["heldout"] == 256
     assert r["heldout_v_rmse"] < r["label_v_std"], r
     assert r["inference_points_per_s"] > 0
+    # the guided screen of the 64 x 64 scan: flagged points are re-run exactly
+    # (the plain map's own values there), so the guided map can only differ
+    # where the calibrated rule trusted the network
+    s = r["screen_scan_64x64"]
+    assert s["grid"] == [64, 64] and 0 <= s["flagged"] <= 4096
+    assert s["path_steps_reruns"] <= s["path_steps_plain_map"]
+    if s["flagged"] == 4096:
+        assert s["max_abs_err"] == 0.0
 
+
+
+def test_poisson_slice_screen():
+    """The 64 x 64 Poisson scan screened by networks of its (F, log Q) slice,
+    at a small size: every grid point within 0.01 of the plain map (all 4096
+    are compared), at fewer path-steps than the plain map, labels included."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_4923_gb300 import box_surrogate
+    r = box_surrogate.slice_screen_64x64(n_label=512, n_hold=256, steps=3000)
+    assert r["frac_within_0.01"] == 1.0, r
+    assert r["ratio_plain_over_guided_total"] > 1.0, r
