@@ -168,7 +168,8 @@ typedef struct {
 /* Batched scan (Sec. 5: many parameter values in one kernel call): all
  * `npts` points (host array, copied) run in one persistent launch over
  * (point, 32-path tile) work items ordered longest first, replayed from a
- * CUDA graph when the shape repeats, and folded per point in a fixed order.
+ * CUDA graph when the shape repeats, or as one launch per point on side
+ * streams (sde_set_scan_mode), and are folded per point in a fixed order.
  * For the inertial model without Poisson noise an item is 64 paths of one
  * point (two paths per GPU lane on packed FP32 pairs); each 32-path tile still
  * writes its own partial sums, so a point's result equals its single run.
@@ -295,6 +296,16 @@ int sde_set_tuning(sde_ctx* ctx, int block_threads, int grid_blocks);
  * Tuning aid with no counterpart in the paper, which runs one path per
  * thread (Algorithm 5). */
 int sde_set_paths_per_thread(sde_ctx* ctx, int paths_per_thread);
+
+/* How sde_scan runs the points of the inertial model: 0 (default) chooses
+ * one point-kernel launch per point when the points have 2048 paths or more
+ * on average (64 such launches side by side fill the GPU) and the persistent
+ * scan kernel otherwise; 1 always the persistent scan kernel; 2 always one
+ * launch per point.  The launches of mode 2 run side by side on side streams of the
+ * context, each with its point's constants as kernel arguments.  Results do
+ * not depend on the mode.  The other models always run one launch per point.
+ * Tuning aid with no counterpart in the paper.  EINVAL outside 0..2. */
+int sde_set_scan_mode(sde_ctx* ctx, int mode);
 
 /* Steps per kernel launch of sde_run / sde_run_paths (Algorithm 5's
  * `samples`): 0 (default) runs the whole simulation in one launch; a

@@ -104,6 +104,7 @@ def lib():
         "sde_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "sde_set_paths_per_thread": (ctypes.c_int, [_P, ctypes.c_int]),
         "sde_set_steps_per_launch": (ctypes.c_int, [_P, ctypes.c_uint64]),
+        "sde_set_scan_mode": (ctypes.c_int, [_P, ctypes.c_int]),
         "sde_occupancy": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
         "sde_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Params), ctypes.c_uint64,
@@ -189,6 +190,10 @@ class Engine:
 
     def set_paths_per_thread(self, ppt=1):
         _check(self._ctx, lib().sde_set_paths_per_thread(self._ctx, int(ppt)))
+
+    def set_scan_mode(self, mode=0):
+        """0: automatic, 1: persistent scan kernel, 2: one point-kernel launch per point."""
+        _check(self._ctx, lib().sde_set_scan_mode(self._ctx, int(mode)))
 
     def set_steps_per_launch(self, steps=0):
         _check(self._ctx, lib().sde_set_steps_per_launch(self._ctx, int(steps)))

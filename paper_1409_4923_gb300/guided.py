@@ -62,17 +62,44 @@ def box_maps(lo, hi, log_mask):
     return (lo + hi) / 2.0, scale
 
 
-def train_ensemble(X, T, shift, scale, log_mask, seeds=(0, 1), steps=8000, batch=512, lr=2e-3):
-    """Two networks on the same labels.  X, T: CUDA float32 [N, 7], [N, 2]."""
+def train_ensemble(X, T, shift, scale, log_mask, seeds=(0, 1), steps=8000, batch=512, lr=2e-3,
+                   concurrent=True):
+    """Networks on the same labels, one per seed.  X, T: CUDA float32 [N, 7], [N, 2].
+    With `concurrent`, each network trains from its own host thread: sde_mlp_fit
+    replays its step graph on a private stream and the binding releases the
+    interpreter lock during the call, so the small, latency-bound kernels of
+    the networks' steps run side by side.  Each network's arithmetic is its
+    own, so the trained parameters do not depend on `concurrent`."""
+    import threading
     t = T.double()
     mean = t.mean(0).cpu().numpy()
     std = t.std(0).clamp_min(1e-6).cpu().numpy()
-    nets, hists = [], []
+    nets = []
     for s in seeds:
         net = S.Surrogate(seed=s)
         net.set_maps(shift, scale, log_mask, mean, std)
-        hists.append(net.fit(X, T, steps=steps, batch=batch, lr=lr, seed=s))
         nets.append(net)
+    hists, errors = [None] * len(nets), []
+
+    def fit(i):
+        try:
+            hists[i] = nets[i].fit(X, T, steps=steps, batch=batch, lr=lr, seed=seeds[i])
+        except Exception as e:        # re-raised below, in the calling thread
+            errors.append(e)
+
+    if concurrent and len(nets) > 1:
+        threads = [threading.Thread(target=fit, args=(i,)) for i in range(len(nets))]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+    else:
+        for i in range(len(nets)):
+            fit(i)
+    if errors:
+        for net in nets:
+            net.close()
+        raise errors[0]
     return nets, hists
 
 

@@ -223,6 +223,7 @@ def test_scan_resume_equals_uninterrupted(E, W):
     pts = _scan_points(E, W, 16, 2048, 2000)          # 1024 items
     eng = E.Engine(0, pts[0]["params"], seed=4)
     try:
+        eng.set_scan_mode(1)                          # the persistent scan kernel
         ref = eng.scan(pts)
         eng.set_tuning(32, 152)                       # 152 warps: about 152 items per launch
         calls = 1

@@ -58,3 +58,29 @@ def test_poisson_slice_screen():
     r = box_surrogate.slice_screen_64x64(n_label=512, n_hold=256, steps=3000)
     assert r["frac_within_0.01"] == 1.0, r
     assert r["ratio_plain_over_guided_total"] > 1.0, r
+
+
+def test_concurrent_training_equals_sequential():
+    """The guided scans train their two networks from two host threads at once;
+    each network's parameters must be those of training it alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import numpy as np
+    from paper_1409_4923_gb300 import guided
+    rng = np.random.default_rng(3)
+    N = 4096
+    X = np.stack([rng.uniform(0.5, 1.5, N), rng.uniform(2, 6, N), rng.uniform(3, 7, N), rng.uniform(-0.3, 0.3, N),
+                  10.0 ** rng.uniform(-4, -1, N), rng.uniform(0.1, 5, N), rng.uniform(0.01, 0.5, N)], axis=1)
+    T = np.stack([np.sin(3 * X[:, 3]) * X[:, 0], -3.0 + 0.1 * X[:, 1]], axis=1)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Td = torch.from_numpy(T.astype(np.float32)).cuda()
+    shift, scale = guided.box_maps(X.min(0), X.max(0), 1 << 4)
+    params = []
+    for concurrent in (True, False):
+        nets, hists = guided.train_ensemble(Xd, Td, shift, scale, 1 << 4, steps=300, batch=256,
+                                            concurrent=concurrent)
+        params.append([n.get_params() for n in nets])
+        for n in nets:
+            n.close()
+    for a, b in zip(*params):
+        assert np.array_equal(a, b)

@@ -126,3 +126,21 @@ def test_scan_device_outputs_equal_host_scan(E, W, flags):
     for i, h in enumerate(host):
         assert list(d[i]) == h["sums"]
         assert list(db[i]) == h["sums"]
+
+
+@pytest.mark.parametrize("flags", [None, 5, 7])
+def test_scan_modes_agree(E, W, flags):
+    """The persistent scan kernel and one point-kernel launch per point (on side
+    streams) give every point's sums bit for bit."""
+    pts = _points(E, W, flags)
+    arg = [dict(p, params=E.make_params(**p["params"])) for p in pts]
+    res = {}
+    for mode in (1, 2):
+        eng = E.Engine(0, arg[0]["params"], seed=11)
+        try:
+            eng.set_scan_mode(mode)
+            res[mode] = eng.scan(arg)
+        finally:
+            eng.close()
+    for a, b in zip(res[1], res[2]):
+        assert a["sums"] == b["sums"]
