@@ -3,6 +3,7 @@
   python -m paper_1409_4923_gb300.profile_cases point dichot_2p20 --paths 1048576 --steps 800 [--ppt 2]
   python -m paper_1409_4923_gb300.profile_cases mlp --rows 1048576 --path 1
   python -m paper_1409_4923_gb300.profile_cases scan --points 256
+  python -m paper_1409_4923_gb300.profile_cases scan_dichot --points 64 --paths 16384 --steps 4096
   python -m paper_1409_4923_gb300.profile_cases fit --rows 16384 --steps 200
 
 Each case runs its launch twice (a warm-up and the one to capture) and
@@ -17,7 +18,7 @@ def main():
     import torch
     from . import engine as E, workloads as W
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["point", "mlp", "scan", "fit"])
+    ap.add_argument("case", choices=["point", "mlp", "scan", "scan_dichot", "fit"])
     ap.add_argument("workload", nargs="?", default="dichot_2p20")
     ap.add_argument("--paths", type=int, default=1 << 20)
     ap.add_argument("--steps", type=int, default=800)
@@ -57,6 +58,18 @@ def main():
             hist = net.fit(x, t, steps=a.steps, batch=a.batch)
             print("loss first/last", float(hist[0]), float(hist[-1]))
         net.close()
+    elif a.case == "scan_dichot":
+        # dichotomous points of equal size through the persistent scan kernel
+        # (two paths per lane), 128-thread blocks
+        pts = [dict(params=E.make_params(**W.dichot_point(b=0.5, F=0.1, point=i)),
+                    dt=W.period_steps(4.9, 200), paths=a.paths, n_transient=0, n_avg=a.steps)
+               for i in range(a.points)]
+        eng = E.Engine(0, pts[0]["params"], seed=0)
+        eng.set_tuning(128, 0)
+        eng.set_scan_mode(1)
+        for _ in range(2):
+            print("mean_v[0]", eng.scan(pts)[0]["mean_v"])
+        eng.close()
     else:
         pts = W.scan_64x64()[:a.points]
         eng = E.Engine(0, E.make_params(**pts[0]["params"]), seed=0)
