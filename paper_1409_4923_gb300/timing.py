@@ -4,10 +4,12 @@
   python -m paper_1409_4923_gb300.timing dichot_reruns   # 256 dichotomous points x 8192 paths
   python -m paper_1409_4923_gb300.timing point poisson_1024 --paths 1048576 --steps 16384
 
-Scans: one persistent launch with the scan autotuner's shape; the first
-repetition captures the scan graph, later ones replay it.  Point runs: CUDA
-events around sde_run on the engine's stream, the best of a few repetitions.
-Orchestration only.
+Scans: the scan autotuner's launch shape, in the mode sde_scan chooses (one
+point-kernel launch per point on side streams when the points hold 2048 paths
+or more on average, else one persistent launch whose graph the first
+repetition captures and later ones replay); wall time around the call, the
+best of the repetitions.  Point runs: CUDA events around sde_run on the
+engine's stream, the best of a few repetitions.  Orchestration only.
 """
 import json
 import time

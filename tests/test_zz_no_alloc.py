@@ -7,7 +7,8 @@ allocation after start-up.  For them the library keeps its scratch in one
 fixed-size device array and the caller passes only the outputs.  This test
 calls that entry point through the C ABI and checks its sums against those
 of the regular entry point (sde_run + sde_stats) on two calls in a row, so the
-second call also shows that the shared array is cleared between calls.  It
+second call also shows that the shared array is cleared between calls, and
+it reads the device's free memory around warm calls, which must not move.  It
 sits in a file of its own that pytest collects last.
 """
 import ctypes
@@ -65,3 +66,29 @@ def test_noalloc_rejects_more_paths_than_its_scratch_holds():
                            ctypes.c_void_p(out5.data_ptr()), None)
     assert rc == E.SDE_EINVAL
     assert b"SDE_NOALLOC_MAX_PATHS" in L.sde_last_error(None)
+
+
+def test_noalloc_warm_calls_leave_free_device_memory_unchanged():
+    """What the entry point is for: after the first call on the device (which
+    loads the library's device code and creates the scratch array), further
+    calls take no device memory.  cudaMemGetInfo's free bytes, read around
+    three calls of the same kind, do not move."""
+    L, E = _lib_and_engine()
+    from paper_1409_4923_gb300 import workloads as W
+    out5 = torch.zeros(5, dtype=torch.float64, device="cuda")
+    p = E.make_params(**W.dichot_point())
+    dt = W.period_steps(4.9, 200)
+
+    def call():
+        rc = L.sde_run_noalloc(0, ctypes.byref(p), 1, 8192, dt, 64, 512, None,
+                               ctypes.c_void_p(out5.data_ptr()), None)
+        assert rc == E.SDE_OK, L.sde_last_error(None)
+        torch.cuda.synchronize()
+
+    call()                                                  # first call: set-up
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert out5[0].item() == 8192
