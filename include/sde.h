@@ -299,9 +299,10 @@ int sde_set_paths_per_thread(sde_ctx* ctx, int paths_per_thread);
 
 /* How sde_scan runs the points of the inertial model: 0 (default) chooses
  * one point-kernel launch per point when the points have 2048 paths or more
- * on average (64 such launches side by side fill the GPU) and the persistent
- * scan kernel otherwise; 1 always the persistent scan kernel; 2 always one
- * launch per point.  The launches of mode 2 run side by side on side streams of the
+ * on average (64 such launches side by side fill the GPU) and no deadline is
+ * given, and the persistent scan kernel otherwise; 1 always the persistent
+ * scan kernel; 2 always one launch per point.  With one launch per point a
+ * deadline bounds each launch's device time from that launch's own start.  The launches of mode 2 run side by side on side streams of the
  * context, each with its point's constants as kernel arguments.  Results do
  * not depend on the mode.  The other models always run one launch per point.
  * Tuning aid with no counterpart in the paper.  EINVAL outside 0..2. */

@@ -636,8 +636,11 @@ static int scan_impl(sde_ctx* c, const sde_scan_point* pts, uint32_t npts, sde_s
     const bool inertial_scan = c->model == SDE_INERTIAL_WASHBOARD && !(flags & SDE_GAUSS_NORMAL);
     uint64_t sum_paths = 0;
     for (uint32_t i = 0; i < npts; ++i) sum_paths += pts[i].paths;
+    // A deadline bounds each kernel's time from its own start, so a scan with a
+    // deadline stays in the one persistent launch unless mode 2 is asked for.
     const bool use_scan_kernel =
-        inertial_scan && (c->scan_mode == 1 || (c->scan_mode == 0 && sum_paths < kPointScanMinPaths * npts));
+        inertial_scan && (c->scan_mode == 1 ||
+                          (c->scan_mode == 0 && (budget > 0 || sum_paths < kPointScanMinPaths * npts)));
     const int point_ppt = inertial_scan ? ((flags & SDE_NOISE_POISSON) ? 1 : 2) : c->paths_per_thread;
     // Without Poisson noise the scan kernel takes two paths per lane: a work
     // item is 64 paths of one point and writes the partial records of its two
