@@ -105,15 +105,18 @@ def test_deadline_times_out_and_context_survives(E, W):
         eng.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("flags", [None, 5])
-def test_scan_device_outputs_equal_host_scan(E, W, flags):
+def test_scan_device_outputs_equal_host_scan(E, W, flags, mode):
     """sde_scan_device leaves each point's five sums in a device array (no host
     round trip): the same values as sde_scan, bit for bit, also when the two
-    calls alternate (each keeps its own captured graph)."""
+    calls alternate (each keeps its own captured graph), in both scan modes
+    (the persistent kernel and one launch per point on side streams)."""
     pts = _points(E, W, flags)
     arg = [dict(p, params=E.make_params(**p["params"])) for p in pts]
     eng = E.Engine(0, arg[0]["params"], seed=4)
     try:
+        eng.set_scan_mode(mode)
         out5 = torch.full((5 * len(arg),), float("nan"), dtype=torch.float64, device="cuda")
         eng.scan_device(arg, out5)
         host = eng.scan(arg)
