@@ -155,7 +155,7 @@ class DichotGuidedScan:
     grid (F in [-0.3, 0.3], b in [0, 2], other parameters as the 2^20-path
     workload), run stage by stage so that every stage can be timed."""
 
-    def __init__(self, nx=1024, ny=1024, label_paths=4096, rerun_paths=8192, spp=200,
+    def __init__(self, nx=1024, ny=1024, label_paths=2048, rerun_paths=8192, spp=200,
                  transient=200, periods=2000, seed=0):
         import torch
         self.nx, self.ny = nx, ny
@@ -234,7 +234,7 @@ class DichotGuidedScan:
         return scan_stats(self.eng, pts) if pts else (np.zeros(0), np.zeros(0))
 
 
-def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=4096, rerun_paths=8192,
+def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=2048, rerun_paths=8192,
                        spp=200, transient=200, periods=2000, tol=0.01, se_tol=0.005, n_valid=2048,
                        seed=0, steps=64000, valid_stream=13, coverage=0.999, log=print):
     """The surrogate-guided scan against plain Monte Carlo on a random sample of
@@ -305,7 +305,7 @@ def main():
                                              "model against plain Monte Carlo")
     ap.add_argument("--grid", type=int, default=1024)
     ap.add_argument("--labels", type=int, default=16384)
-    ap.add_argument("--label-paths", type=int, default=4096)
+    ap.add_argument("--label-paths", type=int, default=2048)
     ap.add_argument("--rerun-paths", type=int, default=8192)
     ap.add_argument("--periods", type=int, default=2000)
     ap.add_argument("--transient", type=int, default=200)
