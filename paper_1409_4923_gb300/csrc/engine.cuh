@@ -438,18 +438,39 @@ constexpr uint32_t kKickWordsPerWarp = kKickWordsPerLane * 32u;
 template <bool POIS, int GAUSS>
 struct WindowedKicks { static constexpr bool value = POIS && GAUSS != kGaussNormal; };
 
+// Two inertial paths per lane keep a kick window per path slot, each of
+// kKick2Chunks chunks (256 steps) and a queue of kKick2Queue increments, so
+// that a warp's two windows (6.4 KB) leave room for 24 warps per SM.  A queue
+// this short does not guarantee that one chunk always fits: a warp in which
+// some lane draws more kicks within the next chunk than its queue holds takes
+// that chunk with the events drawn per chunk, as without windows (the same
+// arithmetic).  At lambda dt = 0.1 a path has 3.2 kicks per chunk on average
+// and more than 16 about once in 10^7 chunks.
+constexpr uint32_t kKick2Chunks = 8;
+constexpr uint32_t kKick2Queue = 16;
+constexpr uint32_t kKick2WordsPerLane = kKick2Chunks + kKick2Queue + 1u;   // per path slot
+constexpr uint32_t kKick2WordsPerWarp = 2u * kKick2WordsPerLane * 32u;
+
+template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
+struct WindowedKicks2 {
+    static constexpr bool value = PPT == 2 && MODEL == kModelInertial && POIS && GAUSS != kGaussNormal;
+};
+
 // Kicks of one path in the steps [n0, wend) into the lane's words tw (stride
 // 32): masks in words 0 .. kKickWinChunks - 1, increments from word
 // kKickWinChunks.  Returns wend, or the step of the first kick not drawn when
 // the queue filled up first; S then holds that kick as its next event.
+// CH, QUEUE: the window's chunks and the queue's length (the two-path
+// windows below are shorter).
+template <uint32_t CH = kKickWinChunks, uint32_t QUEUE = kKickQueue>
 __device__ __forceinline__ uint32_t window_kicks(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                                  uint32_t path, uint32_t n0, uint32_t wend, uint32_t* tw)
 {
 #pragma unroll
-    for (uint32_t c = 0; c < kKickWinChunks; ++c) tw[c * 32u] = 0u;
-    float* tq = (float*)(tw + kKickWinChunks * 32u);
+    for (uint32_t c = 0; c < CH; ++c) tw[c * 32u] = 0u;
+    float* tq = (float*)(tw + CH * 32u);
     uint32_t cnt = 0u;
-    while (S.eP < wend && cnt < kKickQueue) {
+    while (S.eP < wend && cnt < QUEUE) {
         const uint32_t off = S.eP - n0;
         tw[(off >> 5) * 32u] |= 1u << (off & 31u);
         tq[cnt * 32u] = pois_event(S, P, K, path);
@@ -817,12 +838,16 @@ __device__ __forceinline__ float2 with_jumps2(float2 h1, float2 pj, float2 dg)
     return POIS ? __fadd2_rn(h1, pj) : h1;
 }
 
-template <bool POIS, int DICH, int GAUSS, bool ACC>
+// QUEUE: the kick increments come from the two path slots' window queues
+// tq[p] (stride 32), from index qi[p] on, zq[p] holding each slot's next one.
+template <bool POIS, int DICH, int GAUSS, bool ACC, bool QUEUE = false>
 __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointConsts& P,
                                                const LaunchConsts& K, const uint32_t (&path)[2],
                                                uint32_t n0, float dch, float& dcur, uint4 (&w)[2],
                                                uint32_t (&pm)[2], float (&z0)[2], float (&z1)[2],
-                                               float (&z2)[2], uint32_t (&dm)[2])
+                                               float (&z2)[2], uint32_t (&dm)[2],
+                                               const float* const* tq = nullptr, uint32_t* qi = nullptr,
+                                               float* zq = nullptr)
 {
     const float2 ngdt = make_float2(-P.gdt, -P.gdt), nfdt = make_float2(-P.fdt, -P.fdt);
     const float2 wdt = make_float2(P.wdt, P.wdt), whdt = make_float2(P.whdt, P.whdt);
@@ -841,7 +866,7 @@ __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointCon
         // With Poisson noise the block keeps one 4-step group per iteration:
         // the two paths' kick queues unrolled over 16 steps overflow the
         // instruction cache (measured: half speed, "no instruction" stalls).
-#pragma unroll (POIS ? 1 : 4)
+#pragma unroll ((POIS && !QUEUE) ? 1 : 4)
         for (uint32_t q = 0; q < 4u; ++q) {
             uint32_t r[2];
 #pragma unroll
@@ -856,7 +881,19 @@ __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointCon
                     dxi.x = three_point(r[0], P);
                     dxi.y = three_point(r[1], P);
                 }
-                if (POIS) {
+                if (POIS && QUEUE) {
+                    float pv[2];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const bool kick = (pm[p] & bit) != 0u;
+                        pv[p] = kick ? zq[p] : -P.aP_dt;
+                        if (kick) {
+                            ++qi[p];
+                            zq[p] = tq[p][qi[p] * 32u];
+                        }
+                    }
+                    pj = make_float2(pv[0], pv[1]);
+                } else if (POIS) {
                     float pv[2];
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
@@ -1030,6 +1067,41 @@ __device__ __forceinline__ void chunk_steps_multi(PathState (&S)[PPT], const Poi
     }
 }
 
+// The FP32 window partials move to the FP64 accumulators when the chunk
+// from n ends on a multiple of 256 steps.
+template <bool ACC, int PPT>
+__device__ __forceinline__ void flush_window_sums(PathState (&S)[PPT], uint32_t n)
+{
+    if (ACC && ((n + 32u) & 255u) == 0u) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            S[p].svd += (double)S[p].sv;
+            S[p].sv2d += (double)S[p].sv2;
+            S[p].sv = 0.0f;
+            S[p].sv2 = 0.0f;
+        }
+    }
+}
+
+// The chunk from n with its events drawn before it (chunk_events_multi),
+// then the window flush.
+template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, int PPT>
+__device__ __forceinline__ void chunk_drawn_per_chunk(PathState (&S)[PPT], const PointConsts& P,
+                                                      const LaunchConsts& K, const uint32_t (&path)[PPT],
+                                                      uint32_t lane, uint32_t n, float& dcur, uint4 (&w)[PPT])
+{
+    const float dch = drive_at(n + 1u + lane, P);
+    uint32_t pm[PPT], dm[PPT];
+    float z0[PPT], z1[PPT], z2[PPT];
+    if (chunk_events_multi<POIS, DICH, PPT>(S, P, K, path, n, pm, z0, z1, z2, dm))
+        chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, true, PPT>(S, P, K, path, n, dch, dcur, w, pm, z0, z1,
+                                                                    z2, dm);
+    else
+        chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, false, PPT>(S, P, K, path, n, dch, dcur, w, pm, z0, z1,
+                                                                     z2, dm);
+    flush_window_sums<ACC, PPT>(S, n);
+}
+
 template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, int PPT>
 __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const PointConsts& P,
                                                 const LaunchConsts& K, const uint32_t (&path)[PPT],
@@ -1081,27 +1153,55 @@ __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const Point
                     }
                 }
             }
-        } else
-        for (; n + 32u <= n_end; n += 32u) {
-            const float dch = drive_at(n + 1u + lane, P);
-            uint32_t pm[PPT], dm[PPT];
-            float z0[PPT], z1[PPT], z2[PPT];
-            if (chunk_events_multi<POIS, DICH, PPT>(S, P, K, path, n, pm, z0, z1, z2, dm))
-                chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, true, PPT>(S, P, K, path, n, dch, dcur, w,
-                                                                            pm, z0, z1, z2, dm);
-            else
-                chunk_steps_multi<MODEL, POIS, DICH, GAUSS, ACC, false, PPT>(S, P, K, path, n, dch, dcur,
-                                                                             w, pm, z0, z1, z2, dm);
-            if (ACC && ((n + 32u) & 255u) == 0u) {
+        } else if constexpr (WindowedKicks2<MODEL, POIS, DICH, GAUSS, PPT>::value) {
+            // chunks in windows of up to kKick2Chunks, kicks drawn at the start of each
+            uint32_t* tw0 = win + lane;
+            uint32_t* tw1 = win + kKick2WordsPerLane * 32u + lane;
+            const float* tq[2] = {(const float*)(tw0 + kKick2Chunks * 32u),
+                                  (const float*)(tw1 + kKick2Chunks * 32u)};
+            while (n + 32u <= n_end) {
+                uint32_t wend = n + 32u * min(kKick2Chunks, (n_end - n) >> 5);
+                uint32_t es[2], js[2], w2s[2], w3s[2];
 #pragma unroll
-                for (int p = 0; p < PPT; ++p) {
-                    S[p].svd += (double)S[p].sv;
-                    S[p].sv2d += (double)S[p].sv2;
-                    S[p].sv = 0.0f;
-                    S[p].sv2 = 0.0f;
+                for (int p = 0; p < 2; ++p) {
+                    es[p] = S[p].eP; js[p] = S[p].JP; w2s[p] = S[p].pw2; w3s[p] = S[p].pw3;
+                }
+                const uint32_t c0 = window_kicks<kKick2Chunks, kKick2Queue>(S[0], P, K, path[0], n, wend, tw0);
+                const uint32_t c1 = window_kicks<kKick2Chunks, kKick2Queue>(S[1], P, K, path[1], n, wend, tw1);
+                const uint32_t cover = __reduce_min_sync(0xffffffffu, min(c0, c1));
+                if (cover < wend) {
+                    // some lane's queue filled up: draw again from the saved events
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        S[p].eP = es[p]; S[p].JP = js[p]; S[p].pw2 = w2s[p]; S[p].pw3 = w3s[p];
+                    }
+                    if (cover < n + 32u) {
+                        // more kicks within the next chunk than a queue holds:
+                        // that chunk with its events drawn per chunk
+                        chunk_drawn_per_chunk<MODEL, POIS, DICH, GAUSS, ACC, PPT>(S, P, K, path, lane, n, dcur, w);
+                        n += 32u;
+                        continue;
+                    }
+                    wend = n + ((cover - n) & ~31u);      // the whole chunks every lane covers
+                    window_kicks<kKick2Chunks, kKick2Queue>(S[0], P, K, path[0], n, wend, tw0);
+                    window_kicks<kKick2Chunks, kKick2Queue>(S[1], P, K, path[1], n, wend, tw1);
+                }
+                uint32_t qi[2] = {0u, 0u};
+                float zq[2] = {tq[0][0], tq[1][0]};
+#pragma unroll 1
+                for (const uint32_t* pmw = tw0; n < wend; n += 32u, pmw += 32) {
+                    const float dch = drive_at(n + 1u + lane, P);
+                    uint32_t pm[2] = {pmw[0], pmw[kKick2WordsPerLane * 32u]}, pm_unused[2], dm[2];
+                    float z0[2], z1[2], z2[2];
+                    chunk_events_multi<false, DICH, PPT>(S, P, K, path, n, pm_unused, z0, z1, z2, dm);
+                    chunk_steps_x2<POIS, DICH, GAUSS, ACC, true>(S, P, K, path, n, dch, dcur, w, pm, z0, z1, z2,
+                                                                 dm, tq, qi, zq);
+                    flush_window_sums<ACC, PPT>(S, n);
                 }
             }
-        }
+        } else
+        for (; n + 32u <= n_end; n += 32u)
+            chunk_drawn_per_chunk<MODEL, POIS, DICH, GAUSS, ACC, PPT>(S, P, K, path, lane, n, dcur, w);
     }
     if (n < n_end) {
 #pragma unroll

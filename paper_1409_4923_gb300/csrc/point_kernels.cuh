@@ -25,6 +25,10 @@ __device__ __forceinline__ void point_items(const PointConsts& P, const LaunchCo
         extern __shared__ uint32_t sde_point_smem[];
         win = sde_point_smem + (threadIdx.x >> 5) * kKickWordsPerWarp + lane;
     }
+    if constexpr (WindowedKicks2<MODEL, POIS, DICH, GAUSS, PPT>::value) {
+        extern __shared__ uint32_t sde_point_smem[];
+        win = sde_point_smem + (threadIdx.x >> 5) * kKick2WordsPerWarp;
+    }
     for (;;) {
         const uint32_t item = next_item(counter, status, K, lane, t0, (uint32_t)PPT);
         if (item == 0xffffffffu) break;
@@ -67,10 +71,11 @@ __global__ void __launch_bounds__(128) point_kernel(const __grid_constant__ Poin
 }
 
 // The same loop compiled for six resident blocks of 128 threads (at most 80
-// registers, 24 warps per SM).  Two paths per lane without Poisson noise run
-// here: measured on the 2^20-path dichotomous run, 573 ms against 583 ms at
-// 96 registers (five blocks), 576 ms at 72 and 592 ms at 64, where the
-// spills reach the step loop; uncapped (123 registers, 16 warps) 599 ms.
+// registers, 24 warps per SM).  Two paths per lane run here: without Poisson
+// noise (measured on the 2^20-path dichotomous run before the flip windows,
+// 573 ms against 583 ms at 96 registers (five blocks), 576 ms at 72 and
+// 592 ms at 64, where the spills reach the step loop; uncapped, 123
+// registers and 16 warps, 599 ms), and with Poisson noise in kick windows.
 template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 __global__ void __launch_bounds__(128, 6) point_kernel_capped(const __grid_constant__ PointConsts P,
                                                               const __grid_constant__ LaunchConsts K,
@@ -85,7 +90,8 @@ __global__ void __launch_bounds__(128, 6) point_kernel_capped(const __grid_const
 template <int MODEL, bool POIS, int DICH, int GAUSS, int PPT>
 constexpr auto point_kernel_for()
 {
-    if constexpr (PPT == 2 && !POIS) return point_kernel_capped<MODEL, POIS, DICH, GAUSS, PPT>;
+    if constexpr (PPT == 2 && (!POIS || WindowedKicks2<MODEL, POIS, DICH, GAUSS, PPT>::value))
+        return point_kernel_capped<MODEL, POIS, DICH, GAUSS, PPT>;
     else return point_kernel<MODEL, POIS, DICH, GAUSS, PPT>;
 }
 
@@ -97,6 +103,8 @@ constexpr size_t point_smem_bytes(int block_threads)
         return (size_t)(block_threads / 32) * kWinWordsPerWarp * sizeof(uint32_t);
     if (PPT == 1 && WindowedKicks<POIS, GAUSS>::value)
         return (size_t)(block_threads / 32) * kKickWordsPerWarp * sizeof(uint32_t);
+    if (WindowedKicks2<MODEL, POIS, DICH, GAUSS, PPT>::value)
+        return (size_t)(block_threads / 32) * kKick2WordsPerWarp * sizeof(uint32_t);
     return 0u;
 }
 
