@@ -234,20 +234,20 @@ class DichotGuidedScan:
         return scan_stats(self.eng, pts) if pts else (np.zeros(0), np.zeros(0))
 
 
-def guided_dichot_scan(nx=1024, ny=1024, n_label=16384, label_paths=2048, rerun_paths=8192,
+def guided_dichot_scan(nx=1024, ny=1024, n_label=8192, label_paths=2048, rerun_paths=8192,
                        spp=200, transient=200, periods=2000, tol=0.01, se_tol=0.005, n_valid=2048,
-                       seed=0, steps=64000, valid_stream=13, coverage=0.999, log=print):
+                       seed=0, steps=64000, valid_stream=13, coverage=0.999, log=print, batch=512):
     """The surrogate-guided scan against plain Monte Carlo on a random sample of
     the same grid points (see the module docstring)."""
     import torch
     t_all = time.time()
     g = DichotGuidedScan(nx, ny, label_paths, rerun_paths, spp, transient, periods, seed)
-    n_hold = max(512, n_label // 8)
+    n_hold = max(2048, n_label // 8)          # the calibration's 0.999 quantile needs the sample
     t0 = time.time()
     X, v_lab, se_lab = g.labels(n_label, n_hold)
     t_label = time.time() - t0
     t0 = time.time()
-    Xd, hists = g.train(X, v_lab, se_lab, n_label, steps=steps)
+    Xd, hists = g.train(X, v_lab, se_lab, n_label, steps=steps, batch=batch)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     cal = calibrate(g.nets, Xd[n_label:], v_lab[n_label:], se_lab[n_label:],
@@ -304,7 +304,7 @@ def main():
     ap = argparse.ArgumentParser(description="surrogate-guided <v>(F, b) scan of the dichotomous "
                                              "model against plain Monte Carlo")
     ap.add_argument("--grid", type=int, default=1024)
-    ap.add_argument("--labels", type=int, default=16384)
+    ap.add_argument("--labels", type=int, default=8192)
     ap.add_argument("--label-paths", type=int, default=2048)
     ap.add_argument("--rerun-paths", type=int, default=8192)
     ap.add_argument("--periods", type=int, default=2000)
@@ -312,11 +312,12 @@ def main():
     ap.add_argument("--valid", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=64000)
     ap.add_argument("--coverage", type=float, default=0.999)
+    ap.add_argument("--batch", type=int, default=512)
     a = ap.parse_args()
     torch.cuda.set_device(0)
     r = guided_dichot_scan(nx=a.grid, ny=a.grid, n_label=a.labels, label_paths=a.label_paths,
                            rerun_paths=a.rerun_paths, transient=a.transient, periods=a.periods,
-                           n_valid=a.valid, steps=a.steps, coverage=a.coverage)
+                           n_valid=a.valid, steps=a.steps, coverage=a.coverage, batch=a.batch)
     print(json.dumps(r))
 
 
