@@ -157,7 +157,7 @@ def slice_screen_64x64(n_label=1024, n_hold=256, label_paths=4096, label_periods
     return scr
 
 
-def run(n_label=1 << 17, paths=4096, steps=128000, batch=1024, n_infer=1 << 20, seed=0, log=print,
+def run(n_label=1 << 17, paths=4096, steps=256000, batch=1024, n_infer=1 << 20, seed=0, log=print,
         edge_fraction=0.5, screen=True):
     import torch
     n_hold = n_label // 8
@@ -234,7 +234,7 @@ def main():
     ap = argparse.ArgumentParser(description="surrogate of the Poisson model over its 7-D box")
     ap.add_argument("--labels", type=int, default=1 << 17)
     ap.add_argument("--paths", type=int, default=4096)
-    ap.add_argument("--steps", type=int, default=128000)
+    ap.add_argument("--steps", type=int, default=256000)
     ap.add_argument("--infer", type=int, default=1 << 20)
     ap.add_argument("--slice", action="store_true",
                     help="only the 64 x 64 scan's guided screen with networks of its 2-D slice")
