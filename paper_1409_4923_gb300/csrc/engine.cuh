@@ -501,14 +501,15 @@ __device__ __forceinline__ void single_steps(PathState& S, const PointConsts& P,
 // first block (group); each block (group) draws the next one's words while it
 // integrates, so the Philox multiplies interleave with the step arithmetic,
 // and w returns holding those that follow the chunk.
-// With QUEUE the kick increments come from the lane's window queue tq
-// (stride 32) from index qi on, z0 holding the next one; qi advances.
+// With QUEUE the kick increments come from the lane's window queue (stride
+// 32 words): *qp points at the entry held in *zq, the next kick's increment;
+// each kick advances *qp by one entry and loads the following one.
 template <int MODEL, bool POIS, int DICH, int GAUSS, bool ACC, bool FAST, bool QUEUE = false>
 __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, const LaunchConsts& K,
                                             uint32_t path, uint32_t n0, float dch, float& dcur,
                                             uint4& w, uint32_t pm, float z0, float z1, float z2,
-                                            uint32_t dm, const float* tq = nullptr,
-                                            uint32_t* qi = nullptr, float* zq = nullptr)
+                                            uint32_t dm, const float** qp = nullptr,
+                                            float* zq = nullptr)
 {
     // Without Box-Muller words the chunk is two 16-step blocks of one Philox
     // call each: the block's four groups are unrolled, so each group's word
@@ -533,8 +534,8 @@ __device__ __forceinline__ void chunk_steps(PathState& S, const PointConsts& P, 
                         const bool kick = (pm & (1u << (q * 4u + k))) != 0u;
                         pj = kick ? *zq : -P.aP_dt;
                         if (kick) {
-                            ++*qi;
-                            *zq = tq[*qi * 32u];
+                            *qp += 32;
+                            *zq = **qp;
                         }
                     } else if (POIS) {
                         const bool kick = (pm & (1u << (q * 4u + k))) != 0u;
@@ -635,7 +636,7 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
                     S.eP = e_s; S.JP = j_s; S.pw2 = w2_s; S.pw3 = w3_s;
                     window_kicks(S, P, K, path, n, wend, tw);
                 }
-                uint32_t qi = 0u;
+                const float* qp = tq;
                 float zq = tq[0];
 #pragma unroll 1
                 for (const uint32_t* pmw = tw; n < wend; n += 32u, pmw += 32) {
@@ -644,7 +645,7 @@ __device__ __forceinline__ void run_steps(PathState& S, const PointConsts& P, co
                     float z0, z1, z2;
                     chunk_events<false, DICH>(S, P, K, path, n, pm_unused, z0, z1, z2, dm);
                     chunk_steps<MODEL, POIS, DICH, GAUSS, ACC, true, true>(S, P, K, path, n, dch, dcur, w,
-                                                                           *pmw, z0, z1, z2, dm, tq, &qi,
+                                                                           *pmw, z0, z1, z2, dm, &qp,
                                                                            &zq);
                     if (ACC && ((n + 32u) & 255u) == 0u) {
                         S.svd += (double)S.sv;
@@ -839,15 +840,15 @@ __device__ __forceinline__ float2 with_jumps2(float2 h1, float2 pj, float2 dg)
 }
 
 // QUEUE: the kick increments come from the two path slots' window queues
-// tq[p] (stride 32), from index qi[p] on, zq[p] holding each slot's next one.
+// (stride 32 words): qp[p] points at the entry held in zq[p], the slot's next
+// kick's increment.
 template <bool POIS, int DICH, int GAUSS, bool ACC, bool QUEUE = false>
 __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointConsts& P,
                                                const LaunchConsts& K, const uint32_t (&path)[2],
                                                uint32_t n0, float dch, float& dcur, uint4 (&w)[2],
                                                uint32_t (&pm)[2], float (&z0)[2], float (&z1)[2],
                                                float (&z2)[2], uint32_t (&dm)[2],
-                                               const float* const* tq = nullptr, uint32_t* qi = nullptr,
-                                               float* zq = nullptr)
+                                               const float** qp = nullptr, float* zq = nullptr)
 {
     const float2 ngdt = make_float2(-P.gdt, -P.gdt), nfdt = make_float2(-P.fdt, -P.fdt);
     const float2 wdt = make_float2(P.wdt, P.wdt), whdt = make_float2(P.whdt, P.whdt);
@@ -888,8 +889,8 @@ __device__ __forceinline__ void chunk_steps_x2(PathState (&S)[2], const PointCon
                         const bool kick = (pm[p] & bit) != 0u;
                         pv[p] = kick ? zq[p] : -P.aP_dt;
                         if (kick) {
-                            ++qi[p];
-                            zq[p] = tq[p][qi[p] * 32u];
+                            qp[p] += 32;
+                            zq[p] = *qp[p];
                         }
                     }
                     pj = make_float2(pv[0], pv[1]);
@@ -1186,7 +1187,7 @@ __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const Point
                     window_kicks<kKick2Chunks, kKick2Queue>(S[0], P, K, path[0], n, wend, tw0);
                     window_kicks<kKick2Chunks, kKick2Queue>(S[1], P, K, path[1], n, wend, tw1);
                 }
-                uint32_t qi[2] = {0u, 0u};
+                const float* qp[2] = {tq[0], tq[1]};
                 float zq[2] = {tq[0][0], tq[1][0]};
 #pragma unroll 1
                 for (const uint32_t* pmw = tw0; n < wend; n += 32u, pmw += 32) {
@@ -1195,7 +1196,7 @@ __device__ __forceinline__ void run_steps_multi(PathState (&S)[PPT], const Point
                     float z0[2], z1[2], z2[2];
                     chunk_events_multi<false, DICH, PPT>(S, P, K, path, n, pm_unused, z0, z1, z2, dm);
                     chunk_steps_x2<POIS, DICH, GAUSS, ACC, true>(S, P, K, path, n, dch, dcur, w, pm, z0, z1, z2,
-                                                                 dm, tq, qi, zq);
+                                                                 dm, qp, zq);
                     flush_window_sums<ACC, PPT>(S, n);
                 }
             }
