@@ -2,12 +2,14 @@
 
   python -m paper_1409_4923_gb300.timing scan_64x64      # the 64 x 64 Poisson scan
   python -m paper_1409_4923_gb300.timing dichot_reruns   # 256 dichotomous points x 8192 paths
+  python -m paper_1409_4923_gb300.timing scan_64x64 --mode 1   # the persistent scan kernel
   python -m paper_1409_4923_gb300.timing point poisson_1024 --paths 1048576 --steps 16384
 
 Scans: the scan autotuner's launch shape, in the mode sde_scan chooses (one
 point-kernel launch per point on side streams when the points hold 2048 paths
 or more on average, else one persistent launch whose graph the first
-repetition captures and later ones replay); wall time around the call, the
+repetition captures and later ones replay), or the mode --mode asks for
+(sde_set_scan_mode: 1 persistent, 2 one launch per point); wall time around the call, the
 best of the repetitions.  Point runs: CUDA events around sde_run on the
 engine's stream, the best of a few repetitions.  Orchestration only.
 """
@@ -27,7 +29,7 @@ def _scan_points(name, E, W):
     return [dict(p, params=E.make_params(**p["params"])) for p in pts]
 
 
-def time_scan(name, reps=2):
+def time_scan(name, reps=2, mode=0):
     import torch
     from . import autotune, engine as E, workloads as W
     arg = _scan_points(name, E, W)
@@ -36,6 +38,7 @@ def time_scan(name, reps=2):
     try:
         knobs = autotune.tune_scan(0, arg)
         autotune.apply_tuning(eng, knobs)
+        eng.set_scan_mode(mode)
         eng.scan([dict(p, n_transient=0, n_avg=256) for p in arg[:256]])          # warm-up
         times = []
         for _ in range(max(1, reps)):
@@ -48,7 +51,7 @@ def time_scan(name, reps=2):
     t = min(times)
     return {"workload": name, "points": len(arg), "path_steps": path_steps, "seconds": t,
             "seconds_each": times, "path_steps_per_s": path_steps / t, "points_per_s": len(arg) / t,
-            "launch_shape": knobs, "mean_v_first_last": [res[0]["mean_v"], res[-1]["mean_v"]]}
+            "launch_shape": knobs, "scan_mode": mode, "mean_v_first_last": [res[0]["mean_v"], res[-1]["mean_v"]]}
 
 
 def time_point(workload, paths, steps, reps=5):
@@ -88,12 +91,13 @@ def main():
     ap.add_argument("--paths", type=int, default=1 << 20)
     ap.add_argument("--steps", type=int, default=16384)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2], help="scans: 0 auto, 1 persistent, 2 per point")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.what == "point":
         print(json.dumps(time_point(a.workload, a.paths, a.steps, max(a.reps, 3))))
     else:
-        print(json.dumps(time_scan(a.what, a.reps)))
+        print(json.dumps(time_scan(a.what, a.reps, a.mode)))
 
 
 if __name__ == "__main__":
