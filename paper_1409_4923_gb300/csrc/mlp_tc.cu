@@ -142,17 +142,38 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Raw inputs of row r0 + tid (producer threads 0..127), loaded a tile ahead
-// of their use so that the global-load latency overlaps the tile's work.
-__device__ __forceinline__ void prefetch_inputs(const TcArgs& g, int r0, uint32_t tid, float (&xr)[kIn])
+// Raw inputs of row r0 + lane (lanes 0..15), loaded a tile ahead of their
+// use so that the global-load latency overlaps the tile's work.
+__device__ __forceinline__ void prefetch_inputs(const TcArgs& g, int r0, uint32_t lane, float (&xr)[kIn])
 {
 #pragma unroll
     for (int c = 0; c < kIn; ++c) xr[c] = 0.0f;
-    const int row = r0 + (int)tid;
-    if (tid < (uint32_t)kRows && row < g.M) {
+    const int row = r0 + (int)lane;
+    if (lane < 16u && row < g.M) {
 #pragma unroll
         for (int c = 0; c < kIn; ++c) xr[c] = g.x[(size_t)row * kIn + c];
     }
+}
+
+// 32 TMEM lanes x 16 columns (32-bit) from taddr into v; complete after
+// tmem_wait16 on the same registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+
+// Waits for this thread's tensor-memory loads; the registers of the last one
+// are operands, so that no use of them moves above the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+                 :: "memory");
 }
 
 // Waits for the completion of the mbarrier phase with parity `phase`, for at
@@ -200,7 +221,6 @@ enum { kBarFull = 0, kBarEmpty = 6, kBarAccFull = 12, kBarAccEmpty = 14, kBarDon
 
 constexpr int kL12Threads = 800;      // warps 0-7 drain, 8-23 produce, 24 issues the MMAs
 constexpr int kL12Drain = 256;
-constexpr int kL12Prod = 512;
 constexpr int kL12ChunkArrivals = 256;   // the 8 producer warps of one K-block
 constexpr int kL12Slots = 3;          // A ring: three 16 KB K-block slots, cycled across tiles
 constexpr int kL12OffB = 0;
@@ -209,7 +229,7 @@ constexpr int kL12OffStage = kL12OffA + kL12Slots * kARegion;    // 8 drain warp
 constexpr int kL12OffBar = kL12OffStage + (kL12Drain / 32) * 2048;
 constexpr int kL12OffTslot = kL12OffBar + 192;             // after the 17 mbarriers
 constexpr int kL12OffBias = kL12OffBar + 256;
-constexpr int kL12OffX = kL12OffBias + kN * 4;                   // 2 x 128 x 24 BF16 (tile parity)
+constexpr int kL12OffX = kL12OffBias + kN * 4;                   // 16 producer warps x 16 x 24 BF16
 constexpr int kL12OffW1 = kL12OffX + 2 * kRows * kXStride * 2;    // 256 x 24 BF16
 constexpr int kL12OffB1 = kL12OffW1 + kN * kXStride * 2;
 constexpr int kL12OffMaps = kL12OffB1 + kN * 4;
@@ -281,17 +301,19 @@ __global__ void __launch_bounds__(kL12Threads, 1) mlp_tc_layers12_kernel(const _
 
     if (warp >= 8u && warp < 24u) {
         // producers: input map, then layer 1 one K-block at a time; warp pw
-        // computes rows 16 (pw mod 8) .. + 15 of K-blocks 2 (pw / 8) and 2 (pw / 8) + 1
-        const uint32_t ptid = tid - 256u, pw = warp - 8u;
+        // computes rows 16 (pw mod 8) .. + 15 of K-blocks 2 (pw / 8) and 2 (pw / 8) + 1,
+        // mapping its own 16 input rows (lanes 0-15) into its own 16-row block
+        // of sX, so that the producers need no barrier among themselves
+        const uint32_t pw = warp - 8u;
         const uint32_t wrow = (pw & 7u) * 16u, kb0 = (pw >> 3) * 2u;
         const uint32_t ti = lane & 3u;
+        __nv_bfloat16* sX = (__nv_bfloat16*)(base + kL12OffX) + pw * (16u * kXStride);
         float xr[kIn];
-        prefetch_inputs(g, (int)blockIdx.x * kRows, ptid, xr);
-        for (int i = 0; i < ntile; ++i) {
+        prefetch_inputs(g, (int)blockIdx.x * kRows + (int)wrow, lane, xr);
+        for (int i = 0; i < ntile && ok; ++i) {
             const int r0 = ((int)blockIdx.x + i * (int)gridDim.x) * kRows;
-            __nv_bfloat16* sX = (__nv_bfloat16*)(base + kL12OffX) + (uint32_t)(i & 1) * (kRows * kXStride);
-            if (ptid < (uint32_t)kRows) {
-                const int row = r0 + (int)ptid;
+            if (lane < 16u) {
+                const int row = r0 + (int)wrow + (int)lane;
                 float v[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) v[c] = 0.0f;
@@ -303,18 +325,16 @@ __global__ void __launch_bounds__(kL12Threads, 1) mlp_tc_layers12_kernel(const _
                         v[c] = __fmul_rn(r - smaps[c], smaps[kIn + c]);
                     }
                 }
-                uint4* dst = (uint4*)(sX + ptid * kXStride);
+                uint4* dst = (uint4*)(sX + lane * kXStride);
                 dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
                                     pack_bf16x2(v[6], v[7]));
                 dst[1] = make_uint4(0u, 0u, 0u, 0u);
             }
-            if (!group_agree(ok, 2u, (uint32_t)kL12Prod)) {
-                ok = false;
-                break;
-            }
+            __syncwarp();
             uint32_t af[4];
-            ldsm_x4(smem_addr(sX + (wrow + (lane & 15u)) * kXStride + (lane >> 4) * 8u), af[0], af[1], af[2], af[3]);
-            prefetch_inputs(g, r0 + (int)gridDim.x * kRows, ptid, xr);
+            ldsm_x4(smem_addr(sX + (lane & 15u) * kXStride + (lane >> 4) * 8u), af[0], af[1], af[2], af[3]);
+            __syncwarp();
+            prefetch_inputs(g, r0 + (int)gridDim.x * kRows + (int)wrow, lane, xr);
 #pragma unroll 1
             for (uint32_t kb = kb0; kb < kb0 + 2u; ++kb) {
                 if (!ok) break;
@@ -405,50 +425,55 @@ __global__ void __launch_bounds__(kL12Threads, 1) mlp_tc_layers12_kernel(const _
         const uint32_t stage_a = smem_addr(stage);
         for (int i = 0; i < ntile; ++i) {
             const uint32_t b = (uint32_t)i & 1u;
-            const bool mine = wait_phase(bar0 + 8u * (kBarAccFull + b), (uint32_t)(i >> 1) & 1u);
-            if (!group_agree(mine, 1u, (uint32_t)kL12Drain)) {
+            // each drain warp decides alone: no named barrier follows
+            if (!wait_phase(bar0 + 8u * (kBarAccFull + b), (uint32_t)(i >> 1) & 1u)) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = ((int)blockIdx.x + i * (int)gridDim.x) * kRows + (int)trow;
             const uint32_t taddr = tmem + 256u * b + ((quarter * 32u) << 16);
-#pragma unroll 1
-            for (uint32_t cb = half * (kN / 2); cb < (half + 1u) * (kN / 2); cb += 32u) {
-                uint32_t v[32];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                               "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                               "=r"(v[30]), "=r"(v[31])
-                             : "r"(taddr + cb));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                uint32_t packed[16];
+            // the half's 128 columns in steps of 16, each step's load issued
+            // before the previous step's arithmetic; a 32-column box per two steps
+            const uint32_t c0 = half * (kN / 2);
+            uint32_t va[16], vb[16];
+            tmem_ld16(taddr + c0, va);
+            tmem_wait16(va);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    packed[j] = pack_bf16x2(silu_hb(__uint_as_float(v[2 * j]), sbias[cb + 2 * j]),
-                                            silu_hb(__uint_as_float(v[2 * j + 1]), sbias[cb + 2 * j + 1]));
-                // the previous tensor store has read the staging block
-                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                __syncwarp();
+            for (uint32_t j = 0; j < 8u; ++j) {
+                uint32_t (&cur)[16] = (j & 1u) ? vb : va;
+                uint32_t (&nxt)[16] = (j & 1u) ? va : vb;
+                if (j < 7u) tmem_ld16(taddr + c0 + 16u * (j + 1u), nxt);
+                const uint32_t cb = c0 + 16u * j;
+                uint32_t packed[8];
 #pragma unroll
-                for (uint32_t q = 0; q < 4u; ++q)
-                    *(uint4*)(stage + lane * 64u + ((q ^ ((lane >> 1) & 3u)) << 4)) =
-                        make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                // the box's first row; rows past M are not written, and a box wholly
-                // past M is not issued
-                const int y0 = row - (int)lane;
-                if (lane == 0 && y0 < g.M) {
-                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                                 :: "l"((uint64_t)&tmH), "r"((int)cb), "r"(y0), "r"(stage_a) : "memory");
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                for (int k = 0; k < 8; ++k)
+                    packed[k] = pack_bf16x2(silu_hb(__uint_as_float(cur[2 * k]), sbias[cb + 2 * k]),
+                                            silu_hb(__uint_as_float(cur[2 * k + 1]), sbias[cb + 2 * k + 1]));
+                if ((j & 1u) == 0u) {
+                    // the previous tensor store has read the staging block
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    __syncwarp();
                 }
+#pragma unroll
+                for (uint32_t qq = 0; qq < 2u; ++qq) {
+                    const uint32_t q = 2u * (j & 1u) + qq;
+                    *(uint4*)(stage + lane * 64u + ((q ^ ((lane >> 1) & 3u)) << 4)) =
+                        make_uint4(packed[4 * qq], packed[4 * qq + 1], packed[4 * qq + 2], packed[4 * qq + 3]);
+                }
+                if (j & 1u) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    // the box's first row; rows past M are not written, and a box wholly
+                    // past M is not issued
+                    const int y0 = row - (int)lane;
+                    if (lane == 0 && y0 < g.M) {
+                        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                                     :: "l"((uint64_t)&tmH), "r"((int)(cb - 16u)), "r"(y0), "r"(stage_a) : "memory");
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                }
+                if (j < 7u) tmem_wait16(nxt);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
