@@ -725,13 +725,10 @@ static cudaError_t launch_layers34(const sde_tc::TcArgs& a, int sm_count, cudaSt
 {
     static const EncodeTiledFn encode = lookup_encode_tiled();
     if (!encode) return cudaErrorNotSupported;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sde_tc::mlp_tc_layers34_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             sde_tc::kL34SmemBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // the attribute belongs to the current device: set it on every launch
+    cudaError_t e = cudaFuncSetAttribute(sde_tc::mlp_tc_layers34_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sde_tc::kL34SmemBytes);
+    if (e != cudaSuccess) return e;
     alignas(64) CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)sde_tc::kK, (cuuint64_t)a.M};
     const cuuint64_t strides[1] = {(cuuint64_t)sde_tc::kK * sizeof(__nv_bfloat16)};
@@ -751,13 +748,10 @@ static cudaError_t launch_layers12(const sde_tc::TcArgs& a, int sm_count, cudaSt
 {
     static const EncodeTiledFn encode = lookup_encode_tiled();
     if (!encode) return cudaErrorNotSupported;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sde_tc::mlp_tc_layers12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             sde_tc::kL12SmemBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // the attribute belongs to the current device: set it on every launch
+    cudaError_t e = cudaFuncSetAttribute(sde_tc::mlp_tc_layers12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sde_tc::kL12SmemBytes);
+    if (e != cudaSuccess) return e;
     // h2 [M][256] BF16 written in 32 x 32 boxes from 64-byte-swizzled staging blocks
     alignas(64) CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)sde_tc::kN, (cuuint64_t)a.M};

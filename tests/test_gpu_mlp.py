@@ -327,10 +327,12 @@ def test_tcgen05_forward_matches_mma_path_and_oracle(S):
     assert err.max() < 0.03, err.max()
 
 
-@pytest.mark.parametrize("M", [1, 127, 128, 129, 152 * 128 + 5])
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 200, 152 * 128 + 5])
 def test_tcgen05_forward_edge_sizes(S, M):
-    """One row, a tile short of full, exactly one tile, one row past it, and
-    one more tile than SMs: the fused path agrees with the mma.sync path."""
+    """One row, a tile short of full, exactly one tile, one row past it, a
+    tile whose last 32-row boxes of h2 lie past M (clipped and skipped tensor
+    stores), and one more tile than SMs: the fused path agrees with the
+    mma.sync path."""
     net, p, (shift, scale, mask, osh, osc) = _random_net(S, 12)
     x = _raw_inputs(np.random.default_rng(M), M)
     X = torch.from_numpy(x.astype(np.float32)).cuda()
