@@ -485,6 +485,10 @@ __global__ void guided_flags_kernel(const float* __restrict__ v1, const float* _
 struct sde_mlp {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // back-propagation side branches: weight gradients (side[0]) and bias
+    // gradients (side[1]) run beside the chain of back-propagation GEMMs
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
     std::string err;
     float* w = nullptr;              // FP32 master parameters
     __nv_bfloat16* wb = nullptr;     // BF16 copies
@@ -603,14 +607,45 @@ static cudaError_t weight_grad(sde_mlp* n, const __nv_bfloat16* dH, int ldh, int
 }
 
 // Loss and gradients (into n->grad) for a batch already in n->X (Mp rows).
+// The side streams start after the work enqueued so far on the network's stream.
+static cudaError_t fork_sides(sde_mlp* n)
+{
+    cudaError_t e = cudaEventRecord(n->fork_ev, n->stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(n->side[k], n->fork_ev, 0);
+    return e;
+}
+
+static cudaError_t join_sides(sde_mlp* n)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(n->join_ev[k], n->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(n->stream, n->join_ev[k], 0);
+    }
+    return e;
+}
+
+// Loss, then per layer from the top: the gradient of the layer's output dH
+// feeds three independent products: the weight gradient (split-K GEMM and
+// its fixed-order reduction, in order on side[0], which owns the split-K
+// buffer), the bias gradient (column sums, side[1]) and the back-propagation
+// GEMM to the layer below (the critical path, on the network's stream).  The
+// side streams join the network's stream before it returns; every product
+// is the same as in one stream.
 static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_t Mp, float* loss_dev)
 {
     loss_kernel<<<1, 1024, 0, n->stream>>>(n->Yp, t, M, Mp, n->maps, n->dY, loss_dev, n->loss64);
     cudaError_t e = cudaGetLastError();
     // layer 4
-    if (e == cudaSuccess) e = weight_grad(n, n->dY, kOutPad, kOutPad, n->A[2], kH, kH, Mp, n->grad + oW4);
+    if (e == cudaSuccess) e = fork_sides(n);
     if (e == cudaSuccess) {
-        colsum_kernel<<<1, 32 * kColsumRows, 0, n->stream>>>(n->dY, Mp, kOutPad, kOutPad, n->grad + oB4);
+        cudaStream_t main = n->stream;
+        n->stream = n->side[0];
+        e = weight_grad(n, n->dY, kOutPad, kOutPad, n->A[2], kH, kH, Mp, n->grad + oW4);
+        n->stream = main;
+    }
+    if (e == cudaSuccess) {
+        colsum_kernel<<<1, 32 * kColsumRows, 0, n->side[1]>>>(n->dY, Mp, kOutPad, kOutPad, n->grad + oB4);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -624,9 +659,15 @@ static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_
     for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
         const __nv_bfloat16* below = l == 0 ? n->X : n->A[l - 1];
         const int kin = l == 0 ? kInPad : kH;
-        e = weight_grad(n, n->dH[l], kH, kH, below, kin, kin, Mp, n->grad + oW[l]);
+        e = fork_sides(n);                      // dH[l] is complete
         if (e == cudaSuccess) {
-            colsum_kernel<<<kH / 32, 32 * kColsumRows, 0, n->stream>>>(n->dH[l], Mp, kH, kH, n->grad + oB[l]);
+            cudaStream_t main = n->stream;
+            n->stream = n->side[0];
+            e = weight_grad(n, n->dH[l], kH, kH, below, kin, kin, Mp, n->grad + oW[l]);
+            n->stream = main;
+        }
+        if (e == cudaSuccess) {
+            colsum_kernel<<<kH / 32, 32 * kColsumRows, 0, n->side[1]>>>(n->dH[l], Mp, kH, kH, n->grad + oB[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && l > 0) {
@@ -636,7 +677,8 @@ static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_
             e = gemm<false, true, EPI_BWD_DSILU>(a, 0, n->stream);
         }
     }
-    return e;
+    const cudaError_t ej = join_sides(n);     // always: a capture needs its branches joined
+    return e != cudaSuccess ? e : ej;
 }
 
 extern "C" {
@@ -656,6 +698,9 @@ int sde_mlp_create(sde_mlp** out, uint64_t seed, void* cuda_stream)
     } else {
         n->stream = (cudaStream_t)cuda_stream;
     }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&n->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&n->join_ev[k], cudaEventDisableTiming);
     const size_t P = kNParams;
     if (e == cudaSuccess) e = cudaMalloc(&n->w, P * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->wb, P * sizeof(__nv_bfloat16));
@@ -982,6 +1027,11 @@ void sde_mlp_destroy(sde_mlp* n)
     cudaFree(n->w); cudaFree(n->wb); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2);
     cudaFree(n->maps); cudaFree(n->loss64); cudaFree(n->tc_error);
     if (n->host_loss) cudaFreeHost(n->host_loss);
+    for (int k = 0; k < 2; ++k) {
+        if (n->side[k]) cudaStreamDestroy(n->side[k]);
+        if (n->join_ev[k]) cudaEventDestroy(n->join_ev[k]);
+    }
+    if (n->fork_ev) cudaEventDestroy(n->fork_ev);
     if (n->own_stream) cudaStreamDestroy(n->stream);
     delete n;
 }
