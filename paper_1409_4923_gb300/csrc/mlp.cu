@@ -261,27 +261,43 @@ __global__ void output_map_kernel(const float* __restrict__ yp, uint64_t M,
     y[i] = yp[m * kOutPad + o] * maps[2 * kIn + kOut + o] + maps[2 * kIn + o];
 }
 
-// Loss of the standardised outputs and its gradient dY' = (y' - t') / M
-// (BF16, padded columns zero).  One block; fixed-order reduction.
+// Residual of the standardised outputs r = y' - t' for element i of the
+// padded [Mp][kOutPad] output block (zero in the padding).
+__device__ __forceinline__ float loss_residual(const float* __restrict__ yp, const float* __restrict__ t, uint64_t M,
+                                               const float* __restrict__ maps, uint64_t i, bool& real)
+{
+    const uint64_t m = i / kOutPad;
+    const int o = (int)(i % kOutPad);
+    real = m < M && o < kOut;
+    if (!real) return 0.0f;
+    const float tp = (t[m * kOut + o] - maps[2 * kIn + o]) / maps[2 * kIn + kOut + o];
+    return yp[m * kOutPad + o] - tp;
+}
+
+// The loss's gradient dY' = (y' - t') / M (BF16, padded columns zero), one
+// thread per element: the start of back-propagation.
+__global__ void dy_kernel(const float* __restrict__ yp, const float* __restrict__ t, uint64_t M, uint64_t Mp,
+                          const float* __restrict__ maps, __nv_bfloat16* __restrict__ dY)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Mp * kOutPad) return;
+    bool real;
+    const float r = loss_residual(yp, t, M, maps, i, real);
+    dY[i] = __float2bfloat16_rn(real ? r * (1.0f / (float)M) : 0.0f);
+}
+
+// Loss of the standardised outputs, sum over rows of 0.5 |y' - t'|^2 / M, in
+// FP64.  One block; fixed-order reduction.  It runs beside back-propagation.
 __global__ void __launch_bounds__(1024) loss_kernel(const float* __restrict__ yp, const float* __restrict__ t,
                                                     uint64_t M, uint64_t Mp, const float* __restrict__ maps,
-                                                    __nv_bfloat16* __restrict__ dY, float* __restrict__ loss_out,
-                                                    double* __restrict__ loss64)
+                                                    float* __restrict__ loss_out, double* __restrict__ loss64)
 {
     __shared__ double red[1024];
     double s = 0.0;
-    const float invM = 1.0f / (float)M;
     for (uint64_t i = threadIdx.x; i < Mp * kOutPad; i += blockDim.x) {
-        const uint64_t m = i / kOutPad;
-        const int o = (int)(i % kOutPad);
-        float d = 0.0f;
-        if (m < M && o < kOut) {
-            const float tp = (t[m * kOut + o] - maps[2 * kIn + o]) / maps[2 * kIn + kOut + o];
-            const float r = yp[m * kOutPad + o] - tp;
-            s += 0.5 * (double)r * (double)r;
-            d = r * invM;
-        }
-        dY[i] = __float2bfloat16_rn(d);
+        bool real;
+        const float r = loss_residual(yp, t, M, maps, i, real);
+        if (real) s += 0.5 * (double)r * (double)r;
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -625,7 +641,7 @@ static cudaError_t join_sides(sde_mlp* n)
     return e;
 }
 
-// Loss, then per layer from the top: the gradient of the layer's output dH
+// dY, then per layer from the top: the gradient of the layer's output dH
 // feeds three independent products: the weight gradient (split-K GEMM and
 // its fixed-order reduction, in order on side[0], which owns the split-K
 // buffer), the bias gradient (column sums, side[1]) and the back-propagation
@@ -634,10 +650,14 @@ static cudaError_t join_sides(sde_mlp* n)
 // is the same as in one stream.
 static cudaError_t backward_rows(sde_mlp* n, const float* t, uint64_t M, uint64_t Mp, float* loss_dev)
 {
-    loss_kernel<<<1, 1024, 0, n->stream>>>(n->Yp, t, M, Mp, n->maps, n->dY, loss_dev, n->loss64);
+    dy_kernel<<<nblk(Mp * kOutPad), 256, 0, n->stream>>>(n->Yp, t, M, Mp, n->maps, n->dY);
     cudaError_t e = cudaGetLastError();
-    // layer 4
+    // layer 4; the loss value itself on side[1], before the bias gradients
     if (e == cudaSuccess) e = fork_sides(n);
+    if (e == cudaSuccess) {
+        loss_kernel<<<1, 1024, 0, n->side[1]>>>(n->Yp, t, M, Mp, n->maps, loss_dev, n->loss64);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         cudaStream_t main = n->stream;
         n->stream = n->side[0];
