@@ -32,7 +32,10 @@
 //              4's dot products and the outputs (layers 3-4).
 //
 // The accumulator alternates between two 256-column halves of tensor memory,
-// so the MMAs of tile t + 1 run while tile t is drained.  The arithmetic is
+// so the MMAs of tile t + 1 run while tile t is drained.  The layers 3-4 grid
+// is a programmatic dependent launch of the layers 1-2 grid: its CTAs load
+// their weights as SMs free up and wait (griddepcontrol.wait) for the first
+// grid before they read h2.  The arithmetic is
 // that of the layer-by-layer path (BF16 weights and activations, FP32
 // accumulation and biases) except for the SiLU, evaluated through tanh (see
 // silu_hb).
@@ -294,6 +297,8 @@ __global__ void __launch_bounds__(kL12Threads, 1) mlp_tc_layers12_kernel(const _
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    // the layers 3-4 grid may start its prologue as SMs free up
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t sA_a = smem_addr(sA), sB_a = smem_addr(sB);
     const int tiles = (g.M + kRows - 1) / kRows;
     const int ntile = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -557,6 +562,9 @@ __global__ void __launch_bounds__(kL34Threads, 1) mlp_tc_layers34_kernel(const _
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    // h2 is read only after the layers 1-2 grid has completed (programmatic
+    // dependent launch: this prologue may overlap that grid's last tiles)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t sA_a = smem_addr(base + kL34OffA), sB_a = smem_addr(sB);
     const int tiles = (g.M + kRows - 1) / kRows;
     const int ntile = (int)blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -740,8 +748,19 @@ static cudaError_t launch_layers34(const sde_tc::TcArgs& a, int sm_count, cudaSt
         return cudaErrorInvalidValue;
     const int tiles = (a.M + sde_tc::kRows - 1) / sde_tc::kRows;
     const int grid = tiles < sm_count ? tiles : sm_count;
-    sde_tc::mlp_tc_layers34_kernel<<<grid, sde_tc::kL34Threads, sde_tc::kL34SmemBytes, st>>>(a, tm);
-    return cudaGetLastError();
+    // programmatic dependent launch: the kernel waits for the layers 1-2 grid
+    // (griddepcontrol.wait) before it reads h2
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)sde_tc::kL34Threads);
+    cfg.dynamicSmemBytes = (size_t)sde_tc::kL34SmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sde_tc::mlp_tc_layers34_kernel, a, tm);
 }
 
 static cudaError_t launch_layers12(const sde_tc::TcArgs& a, int sm_count, cudaStream_t st)
