@@ -233,7 +233,7 @@ constexpr int kL12OffBar = kL12OffStage + (kL12Drain / 32) * 2048;
 constexpr int kL12OffTslot = kL12OffBar + 192;             // after the 17 mbarriers
 constexpr int kL12OffBias = kL12OffBar + 256;
 constexpr int kL12OffX = kL12OffBias + kN * 4;                   // 16 producer warps x 16 x 24 BF16
-constexpr int kL12OffW1 = kL12OffX + 2 * kRows * kXStride * 2;    // 256 x 24 BF16
+constexpr int kL12OffW1 = kL12OffX + 16 * 16 * kXStride * 2;      // 256 x 24 BF16
 constexpr int kL12OffB1 = kL12OffW1 + kN * kXStride * 2;
 constexpr int kL12OffMaps = kL12OffB1 + kN * 4;
 constexpr int kL12SmemBytes = kL12OffMaps + 64 * 4 + 1024;
@@ -243,12 +243,14 @@ static_assert(kL12SmemBytes <= 227 * 1024, "shared memory");
 // Input map and layers 1-2.  Warps 8-23 produce the A tile: warp w computes
 // rows 16 ((w - 8) mod 8) .. + 15 of the K-blocks 2 ((w - 8) / 8) and that
 // plus one (layer 1 on mma.sync, one K step over the 7 inputs and zero
-// padding), SiLU, BF16, written by stmatrix into the block's slot of a ring
-// of three slots cycled across tiles.  Warp 24 issues the MMAs.  Warps 0-7
-// drain (warp w: lane quarter w mod 4, column half w / 4) and write h2 32 x 32
-// at a time through a 2 KB staging block in the 64-byte swizzle, which a TMA
-// tensor store copies to global memory (one 16-byte store per lane and row
-// would touch 32 cache lines per instruction).
+// padding; each warp maps its own 16 input rows), SiLU, BF16, written by
+// stmatrix into the block's slot of a ring of three slots cycled across
+// tiles.  Warp 24 issues the MMAs.  Warps 0-7 drain (warp w: lane quarter
+// w mod 4, column half w / 4; each 16-column load issued before the previous
+// step's arithmetic) and write h2 32 x 32 at a time through a 2 KB staging
+// block in the 64-byte swizzle, which a TMA tensor store copies to global
+// memory (one 16-byte store per lane and row would touch 32 cache lines per
+// instruction).
 __global__ void __launch_bounds__(kL12Threads, 1) mlp_tc_layers12_kernel(const __grid_constant__ TcArgs g,
                                                                        const __grid_constant__ CUtensorMap tmH)
 {
