@@ -366,7 +366,7 @@ def scan_record(n_valid, device_index):
         "guided_over_plain_points_per_s": g["points_per_s_guided"] / plain_pps,
         "scan_64x64": {"workload": "4096 Poisson points, 64 x 64 grid of F x log Q, paths 256..16384, "
                                    "500..3000 averaged periods, one point-kernel launch per point on "
-                                   "64 side streams",
+                                   "128 side streams",
                        "seconds": s64["seconds"], "points_per_s": s64["points_per_s"],
                        "path_steps_per_s": s64["path_steps_per_s"],
                        "launch_shape": s64["launch_shape"]},
